@@ -1,0 +1,132 @@
+"""Physics pins of the oracle's force term (Sec. 2.2) that the moment
+identities cannot see:
+
+* mechanical equilibrium: on the exact square-gradient planar profile of the
+  vdW fluid (Sec. 4.1, the interface-profile integral) the force density
+  rho T B balances the kinetic pressure gradient, which fixes B, Lambda
+  (Eq. 19) and P^w (Eq. 18) together;
+* heat conduction: C_q (Eq. 23) sets the Prandtl number Pr = tau / 2(tau - q)
+  (Sec. 2.2), i.e. the thermal diffusivity T (tau - q) of the 2-D model;
+  the entropy mode of an ideal gas must decay at that rate.
+Planted mistakes are planted in private copies of the oracle."""
+import importlib.util
+import os
+import sys
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+from oracle import fftlb_oracle as O
+from oracle import thermo as TH
+
+ORACLE_SRC = os.path.join(os.path.dirname(O.__file__), "fftlb_oracle.py")
+
+
+def planted(old, new):
+    src = open(ORACLE_SRC).read()
+    assert old in src
+    spec = importlib.util.spec_from_loader("oracle_planted_phys", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules["oracle_planted_phys"] = mod
+    exec(src.replace(old, new), mod.__dict__)
+    return mod
+
+
+def planar_profile(T, a, b, K, dx, N):
+    """Periodic slab built from the exact square-gradient profile: solves
+    K rho'' = mu(rho) - mu_s from the mid density outwards (first integral
+    K rho'^2 / 2 = Delta omega), liquid in the middle half."""
+    rv, rl = TH.maxwell(T, a, b)
+    mu_s = TH.chem_potential(rv, T, a, b)
+    rm = 0.5 * (rv + rl)
+    d0 = np.sqrt(2 * TH.delta_omega(rm, T, a, b, rv, rl) / K)
+    fun = lambda z, y: [y[1], (TH.chem_potential(y[0], T, a, b) - mu_s) / K]
+    hi = lambda z, y: y[0] - (rl - 1e-12)
+    lo = lambda z, y: y[0] - (rv + 1e-12)
+    hi.terminal = lo.terminal = True
+    kw = dict(method="DOP853", rtol=1e-13, atol=1e-16, events=[hi, lo], dense_output=True)
+    fw = solve_ivp(fun, [0, 10.0], [rm, d0], **kw)
+    bw = solve_ivp(fun, [0, -10.0], [rm, d0], **kw)
+
+    def prof(z):
+        out = np.empty_like(z)
+        m = z >= 0
+        out[m] = np.where(z[m] > fw.t[-1], rl, fw.sol(np.clip(z[m], 0, fw.t[-1]))[0])
+        out[~m] = np.where(z[~m] < bw.t[-1], rv, bw.sol(np.clip(z[~m], bw.t[-1], 0))[0])
+        return out
+
+    x = np.arange(N) * dx
+    L = N * dx
+    assert fw.t[-1] < L / 4 and -bw.t[-1] < L / 4
+    return np.where(x < L / 2, prof(x - L / 4), prof(3 * L / 4 - x))
+
+
+def mech_residual(mod, window=0):
+    a, b, T, K, dx, N = 9 / 8, 1 / 3, 0.95, 1e-4, 1 / 256, 512
+    rho = np.tile(planar_profile(T, a, b, K, dx, N), (2, 1))
+    z = np.zeros_like(rho)
+    p = mod.Params(nx=N, ny=2, dx=dx, a=a, b=b, K=K, q=-0.004, window=window)
+    f = mod.init_equilibrium(rho, z, z, np.full_like(rho, T), p)
+    _, parts = mod.rhs(f, p, return_parts=True)
+    rx = O.D(rho, "x", dx, window)
+    res = rho * T * parts["Bx"] + T * rx
+    return np.abs(res).max() / np.abs(T * rx).max(), np.abs(parts["By"]).max()
+
+
+def test_planar_vdw_profile_is_in_mechanical_equilibrium():
+    r, by = mech_residual(O)
+    assert r < 1e-5 and by == 0.0
+
+
+@pytest.mark.parametrize("old,new", [
+    ("M * (rho * lap + 0.5 * grad2)", "M * (rho * lap + 1.0 * grad2)"),
+    ("Lxx = M * rx * rx + iso", "Lxx = -M * rx * rx + iso"),
+    ("rho * T / (1.0 - b * rho) - a * rho * rho", "rho * T / (1.0 - b * rho) - 0.5 * a * rho * rho"),
+    ("Bx = (Pix + dLx", "Bx = (Pix - dLx"),
+])
+def test_mechanical_pin_catches_planted_mistakes(old, new):
+    r, _ = mech_residual(planted(old, new))
+    assert r > 1e-2
+
+
+def entropy_mode_rate(mod, q, tau=1e-3, N=16, dx=1 / 256, nsteps=600, every=100):
+    """Decay rate of the entropy perturbation ds = dT/T - drho/rho of an
+    ideal gas (a = b = K = 0) started in pressure balance."""
+    p = mod.Params(nx=N, ny=2, dx=dx, dt=1e-5, tau=tau, a=0.0, b=0.0, K=0.0, q=q,
+                   window=0, integrator=1)
+    x = np.arange(N) * dx
+    k = 2 * np.pi / (N * dx)
+    eps = 1e-3
+    T = np.tile(1.0 + eps * np.cos(k * x), (2, 1))
+    rho = np.tile(1.0 - eps * np.cos(k * x), (2, 1))
+    z = np.zeros_like(T)
+    f = mod.init_equilibrium(rho, z, z, T, p)
+    amps, ts = [], []
+    for s in range(nsteps + 1):
+        if s % every == 0:
+            r, _, _, Tn = mod.moments(f)
+            ds = (Tn[0] - 1.0) - (r[0] - 1.0)
+            amps.append((ds * np.cos(k * x)).sum() * 2 / N)
+            ts.append(s * p.dt)
+        if s < nsteps:
+            f = mod.step(f, p)
+    amps = np.array(amps)
+    if np.any(amps[1:] <= 0):
+        return float("nan"), k
+    return -np.polyfit(ts[1:], np.log(amps[1:]), 1)[0], k
+
+
+def test_heat_conduction_follows_prandtl_relation():
+    tau = 1e-3
+    g0, k = entropy_mode_rate(O, 0.0, tau)
+    gq, _ = entropy_mode_rate(O, -0.004, tau)
+    assert g0 == pytest.approx(tau * k * k, rel=0.2)          # T = 1
+    assert gq / g0 == pytest.approx((tau + 0.004) / tau, rel=0.15)
+
+
+def test_heat_conduction_pin_catches_flipped_Cq():
+    mod = planted("Cq = (Dx(Phx) + Dy(Phy))", "Cq = -(Dx(Phx) + Dy(Phy))")
+    g0, _ = entropy_mode_rate(mod, 0.0)
+    gq, _ = entropy_mode_rate(mod, -0.004)
+    assert not (gq / g0 == pytest.approx(5.0, rel=0.3))
