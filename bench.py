@@ -1,0 +1,331 @@
+"""Benchmark of the FFT-LB hot path: MLUPS (million lattice-site updates per
+second, one update = one full SSP-RK3 time step) on the 1024 x 1024
+spinodal-decomposition workload, plus the roofline fraction of the dominant
+kernel, an end-to-end figure through the C ABI with host buffers, and the
+FP64 oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 32|64]
+    python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload on its own GPU (the single-grid path does not shard).
+"""
+from __future__ import annotations
+
+import os
+
+# the oracle legs run numpy single-threaded; the reported core count is 1
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1011_3582_gb300 import workloads  # noqa: E402
+
+A, B = 9.0 / 49.0, 2.0 / 21.0                # vdW constants of the benchmark set
+TC, RHOC = 8 * A / (27 * B), 1.0 / (3 * B)    # 4/7, 3.5
+METRIC = "MLUPS at 1024^2 (spinodal, SSP-RK3 steps)"
+
+
+def workload_fields(n, seed=7):
+    """rho = rho_c (1 + 0.01 N(0,1)), seed 7, u = 0, T = 0.7 T_c."""
+    return workloads.spinodal(n, n, RHOC, 0.7 * TC, amp=0.01, seed=seed)
+
+
+def workload_params(fl, n, precision, integrator=3):
+    return fl.params(nx=n, ny=n, a=A, b=B, precision=precision, integrator=integrator, window=4)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1011_3582_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, precision, n):
+    """DRAM bytes per launch from profiles/ncu_traffic.txt, valid only for
+    the kernel sources it was captured from (same source hash)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 5 and not line.startswith("#"):
+            k, prec, grid, by, hsh = parts[:5]
+            if k == kernel and prec == str(precision) and grid == str(n) and hsh == cur:
+                return float(by)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 6:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n=1024):
+    """The FP64 oracle on the host: one SSP-RK3 stage of the n x n workload
+    (a third of a step), scaled to MLUPS per full step."""
+    from oracle import fftlb_oracle as O
+    p = O.Params(nx=n, ny=n, a=A, b=B, integrator=3, window=4)
+    f = O.init_equilibrium(*workload_fields(n), p)
+    t0 = time.perf_counter()
+    f = f + p.dt * O.rhs(f, p)
+    dt = time.perf_counter() - t0
+    return {"value": n * n / (3.0 * dt) / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "one SSP-RK3 stage of the %dx%d workload (1/3 step), numpy fp64, %.1f s" % (n, n, dt)}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores; each timed step
+    is one SSP-RK3 stage of a 512 x 512 sample of the workload."""
+    if rank != 0:
+        return
+    from oracle import fftlb_oracle as O
+    n = 512
+    p = O.Params(nx=n, ny=n, a=A, b=B, integrator=3, window=4)
+    f = O.init_equilibrium(*workload_fields(n), p)
+    for _ in range(args.warmup):
+        O.rhs(f, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = f + p.dt * O.rhs(f, p)
+    el = time.perf_counter() - t0
+    v = n * n * args.steps / (3.0 * el) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3.0 * el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "spinodal %dx%d sample of the 1024x1024 workload" % (n, n),
+                                             "grid": n, "integrator": "ssp-rk3", "window": "k4"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d SSP-RK3 stages of a %dx%d sample" % (args.steps, n, n)},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--grid", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 companion measurement")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1011_3582_gb300 import fftlb
+
+    n = args.grid
+    stream = torch.cuda.current_stream()
+    fields = workload_fields(n)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def maxed(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def time_path(precision, steps, warmup, sample_clocks):
+        h = fftlb.Handle(workload_params(fftlb, n, precision), stream=stream.cuda_stream)
+        h.set_fields(*fields)
+        h.step(warmup)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        if sample_clocks:
+            clk.__enter__()
+        ev0.record(stream)
+        h.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if sample_clocks:
+            clk.__exit__()
+        barrier()
+        ms = maxed(ev0.elapsed_time(ev1))
+        # per-kernel timing on a second pass of the same length
+        h.profile(True)
+        h.step(steps)
+        prof = h.profile_read()
+        h.profile(False)
+        inv = h.invariants()
+        lps = h.launches_per_step()
+        h.close()
+        return ms, prof, inv, lps, (clk.summary() if sample_clocks else None)
+
+    ms, prof, inv, lps, clocks = time_path(args.precision, args.steps, args.warmup, True)
+    K = args.steps
+    value = world * n * n * K / (ms * 1e-3) / 1e6
+
+    peaks, peak_kind = measured_peaks()
+    top = max(prof, key=lambda k: prof[k][0])
+    tms, tl, tbytes = prof[top]
+    achieved = tbytes / (tms * 1e-3 / tl) / 1e9
+    traffic = ncu_traffic(top, args.precision, n)
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind,
+                "kernel_share": tms / sum(v[0] for v in prof.values())}
+    step_bytes = sum(prof[k][2] * prof[k][1] for k in prof) / K
+    kernels = {k: {"ms_per_launch": prof[k][0] / max(prof[k][1], 1), "launches": prof[k][1],
+                   "alg_bytes_per_launch": prof[k][2],
+                   "gbs": prof[k][2] / (prof[k][0] * 1e-3 / max(prof[k][1], 1)) / 1e9 if prof[k][0] else None}
+               for k in prof}
+
+    fp64 = None
+    if not args.no_fp64 and args.precision != 64:
+        ms64, prof64, _, _, _ = time_path(64, max(2, K // 4), 3, False)
+        fp64 = {"value": world * n * n * max(2, K // 4) / (ms64 * 1e-3) / 1e6, "unit": "MLUPS",
+                "ms_per_step": ms64 / max(2, K // 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        # public API with pinned host buffers: upload the fields, then each
+        # step: advance one step and read back its invariants (6 doubles);
+        # read the fields back at the end
+        pinned = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
+        for dst, src in zip(pinned, fields):
+            dst[...] = src
+        outs = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
+        h = fftlb.Handle(workload_params(fftlb, n, args.precision), stream=stream.cuda_stream)
+        h.set_fields(*pinned)
+        h.step(2)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        h.set_fields(*pinned)
+        for _ in range(K):
+            h.step(1)
+            h.invariants()
+        h.fields(*outs)
+        el = maxed(time.perf_counter() - t0)
+        h.close()
+        fb = 4 * n * n * 8
+        e2e = {"value": world * n * n * K / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": fb / K,
+               "d2h_bytes_per_step": 48 + fb / K}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+                "config": {"workload": "spinodal decomposition %dx%d, rho = rho_c (1 + 0.01 N(0,1)) seed 7, "
+                                       "T = 0.7 T_c, vdW a = 9/49 b = 2/21" % (n, n),
+                           "grid": n, "integrator": "ssp-rk3", "window": "k4", "dx": 1 / 256, "dt": 1e-5,
+                           "tau": 1e-2, "K": 1e-5, "q": -0.004,
+                           "l2": "inputs larger than L2 (state %.0f MB + spectra %.0f MB)" % (
+                               33 * n * n * args.precision / 8 / 1e6, 58 * n * n * args.precision / 8 / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "kernels": kernels, "alg_bytes_per_step": step_bytes,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
+                "fp64": fp64, "invariants_after": inv}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

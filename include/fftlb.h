@@ -1,0 +1,157 @@
+/*
+ * fftlb.h - C ABI of libfftlb.so, a GB300 (sm_103a) implementation of the
+ * windowed-FFT lattice-Boltzmann method for thermal liquid-vapour systems of
+ * Gan, Xu, Zhang and Li, "FFT-LB modeling of thermal liquid-vapor systems"
+ * (arXiv:1011.3582).
+ *
+ * The problem a handle holds is the paper's: a periodic nx x ny grid with
+ * dx = dy (Sec. 3, periodic boundary conditions), the 33-velocity model of
+ * Sec. 2.1 (Eq. 1), the BGK equation with the Gonnella-Lamura-Sofonea force
+ * term of Sec. 2.2 (Eqs. 10-23) for the van der Waals EOS
+ * P = rho T / (1 - b rho) - a rho^2 (Eq. 18 with general a, b), and every
+ * spatial derivative taken by the windowed FFT of Sec. 3.6 (Eqs. FT, IFT,
+ * FFT, K1-K4).
+ *
+ * Conventions shared by every call:
+ *  - Fields are row-major [ny][nx] (x fastest).  The distribution function is
+ *    [33][ny][nx], velocity j in the order of Eq. 1: j = 0 is v_0 = 0, and
+ *    j = 1 + 8 (k-1) + (i-1) is v_ki = v_k (cos((i-1) pi/4), sin((i-1) pi/4)).
+ *  - Host/device: a pointer argument is host memory unless the call's
+ *    `on_device` flag is non-zero, in which case it is device memory on the
+ *    handle's device.  The caller owns every buffer it passes; the library
+ *    reads or writes it only during the call (asynchronously on the handle's
+ *    stream for device pointers; host copies are complete when the call
+ *    returns).
+ *  - Streams: the handle works on the CUDA stream passed to fftlb_create
+ *    (borrowed, not owned; NULL = the legacy default stream).
+ *  - Errors: every call returns an fftlb_status; none aborts, traps or prints.
+ *    fftlb_last_error(h) gives a message for the last failing call on h.
+ *  - Memory: fftlb_create allocates all device memory the handle needs
+ *    (cudaMalloc) and fftlb_destroy frees it; no other call allocates.
+ */
+#ifndef FFTLB_H
+#define FFTLB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftlb_s *fftlb_t;
+
+typedef enum {
+    FFTLB_OK = 0,
+    FFTLB_ERR_ARG = 1,      /* invalid argument (sizes, parameters, NULL) */
+    FFTLB_ERR_OOM = 2,      /* device allocation failed */
+    FFTLB_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    FFTLB_ERR_UNSTABLE = 4, /* non-finite or unphysical state detected */
+    FFTLB_ERR_TIMEOUT = 5,  /* a bounded device wait ran out */
+    FFTLB_ERR_STATE = 6     /* call not valid in the handle's state */
+} fftlb_status;
+
+/* Problem parameters (Sec. 2.2, Sec. 3; paper defaults in brackets).
+ *  nx, ny      grid; each an even 2^p 3^q with 4 <= n <= 1024 (fp64) or
+ *              <= 2048 (fp32)
+ *  dx          lattice spacing, dx = dy [1/256]
+ *  dt          time step [1e-5]
+ *  tau         BGK relaxation time (Eq. 2) [1e-2]
+ *  a, b        vdW constants of P^w (Eq. 18) [9/8, 1/3]
+ *  K, H        M = K + H T (Eq. 19) [1e-5, 0]
+ *  q           heat-flux parameter of C_q (Eq. 23) [-0.004]
+ *  zeta        bulk viscosity (Eqs. 21, 22) [0]
+ *  window      0 = exact k; 1..4 = k_1..k_4 of Eqs. K1-K4 [4]
+ *  integrator  1 = forward Euler, 3 = SSP-RK3 (Shu-Osher)
+ *  precision   64 = everything in fp64; 32 = FFTs and pointwise in fp32
+ *              (conservation sums still fp64)
+ *  check_every fftlb_step checks the state for non-finite or unphysical
+ *              values every check_every steps (0 = never)
+ */
+typedef struct {
+    int nx, ny;
+    double dx, dt, tau, a, b, K, H, q, zeta;
+    int window, integrator, precision, check_every;
+} fftlb_params;
+
+/* Velocity set of Eq. 1: nspeeds rings of ndirs directions.  Only
+ * nspeeds = 4, ndirs = 8 is supported; speeds = NULL selects the paper's
+ * (1.0, 1.9, 2.9, 4.3). */
+typedef struct {
+    int nspeeds;
+    const double *speeds;
+    int ndirs;
+} fftlb_velset;
+
+/* Create a handle for problem *p on the current CUDA device.  velset may be
+ * NULL (paper's set).  cuda_stream is a cudaStream_t (may be NULL).
+ * Allocates ~ (2*33 + 38 + 15 + 5 + 7) nx ny values of the chosen precision.
+ * Errors: FFTLB_ERR_ARG (sizes, tau <= 0, window, integrator, precision),
+ * FFTLB_ERR_OOM, FFTLB_ERR_CUDA.  On error *h is set to NULL. */
+fftlb_status fftlb_create(fftlb_t *h, const fftlb_params *p,
+                          const fftlb_velset *velset, void *cuda_stream);
+
+/* Set f = f^eq(rho, u, T) (Eq. 3) from fp64 fields [ny][nx] and reset the
+ * step counter.  Requires rho > 0, T > 0 and b rho < 1 where checked. */
+fftlb_status fftlb_set_fields(fftlb_t h, const double *rho, const double *ux,
+                              const double *uy, const double *T, int on_device);
+
+/* Advance nsteps time steps (each: 1 stage for Euler, 3 for SSP-RK3),
+ * asynchronously on the handle's stream, except that every check_every
+ * steps the state is checked (which synchronises).  *steps_done (may be
+ * NULL) receives the steps completed; on FFTLB_ERR_UNSTABLE it is the step
+ * after which the bad state was seen. */
+fftlb_status fftlb_step(fftlb_t h, long nsteps, long *steps_done);
+
+/* Moments rho, u_x, u_y, T of the current f (Eqs. 7-9), as fp64 [ny][nx].
+ * Any output pointer may be NULL.  Host outputs: synchronises. */
+fftlb_status fftlb_fields(fftlb_t h, double *rho, double *ux, double *uy,
+                          double *T, int on_device);
+
+/* The full state f as fp64 [33][ny][nx] (get) or replace it (set). */
+fftlb_status fftlb_get_f(fftlb_t h, double *f, int on_device);
+fftlb_status fftlb_set_f(fftlb_t h, const double *f, int on_device);
+
+/* Conservation sums in fp64 (Eqs. 12-17): out[0] = mass sum rho dx^2,
+ * out[1], out[2] = momentum sum rho u dx^2, out[3] = total energy
+ * sum e_T dx^2 with e_T = rho T - a rho^2 + K |grad rho|^2 / 2 + rho u^2 / 2
+ * (grad rho by the windowed FFT), out[4] = max |u| (spurious velocity),
+ * out[5] = simulated time steps * dt.  Synchronises the stream. */
+fftlb_status fftlb_invariants(fftlb_t h, double out[6]);
+
+/* Windowed spectral derivatives of caller fields (Sec. 3.6, Fig. 3; Eqs. FT,
+ * IFT, FFT, K1-K4) using the handle's grid, dx and window: for each of
+ * nfields real device fields g[nfields][ny][nx] (fp64) writes
+ *   out[2*i]   = D_x g_i,   out[2*i+1] = D_y g_i   (device, fp64).
+ * Uses the handle's scratch buffers (the handle's state f is untouched).
+ * 1 <= nfields <= 16. */
+fftlb_status fftlb_gradient(fftlb_t h, const double *g, double *out, int nfields);
+
+/* Checkpoint: write / read f, the step count and the parameters (binary,
+ * little-endian, with a format version).  fftlb_load requires a handle
+ * created with the same nx, ny and precision. */
+fftlb_status fftlb_save(fftlb_t h, const char *path);
+fftlb_status fftlb_load(fftlb_t h, const char *path);
+
+/* Free all device memory of h.  h may be NULL. */
+fftlb_status fftlb_destroy(fftlb_t h);
+
+/* Message of the last failing call on h (h may be NULL for errors from
+ * fftlb_create).  Valid until the next call on the same thread. */
+const char *fftlb_last_error(fftlb_t h);
+
+/* Number of kernel launches issued by one time step (for accounting). */
+int fftlb_launches_per_step(fftlb_t h);
+
+/* Kernel timing.  fftlb_profile(h, 1) clears the counters and from then on
+ * records a pair of CUDA events on the handle's stream around every launch
+ * of a time step; fftlb_profile(h, 0) stops.  fftlb_profile_read fills, for
+ * kernel kind k < nkinds (at most 6: see fftlb_kernel_name), the summed
+ * device milliseconds ms[k], the launch count launches[k] and the
+ * algorithmic bytes of one launch bytes[k] (each value the kernel must read
+ * or write, counted once); any array may be NULL.  Synchronises. */
+fftlb_status fftlb_profile(fftlb_t h, int enable);
+fftlb_status fftlb_profile_read(fftlb_t h, double *ms, long *launches, double *bytes, int nkinds);
+const char *fftlb_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTLB_H */

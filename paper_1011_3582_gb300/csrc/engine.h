@@ -1,0 +1,62 @@
+// Precision-independent interface between the C ABI (api.cu) and the
+// templated engine (engine_impl.cuh, instantiated in engine_f64.cu and
+// engine_f32.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <string>
+
+#include "../../include/fftlb.h"
+
+namespace fftlb {
+
+struct Status {
+    fftlb_status code = FFTLB_OK;
+    std::string msg;
+    static Status ok() { return Status(); }
+    static Status err(fftlb_status c, const std::string &m) {
+        Status s;
+        s.code = c;
+        s.msg = m;
+        return s;
+    }
+    bool good() const { return code == FFTLB_OK; }
+};
+
+class Engine {
+  public:
+    virtual ~Engine() {}
+    virtual Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s) = 0;
+    virtual Status set_fields(const double *rho, const double *ux, const double *uy, const double *T,
+                              bool on_device) = 0;
+    virtual Status step(long nsteps, long *done) = 0;
+    virtual Status fields(double *rho, double *ux, double *uy, double *T, bool on_device) = 0;
+    virtual Status get_f(double *f, bool on_device) = 0;
+    virtual Status set_f(const double *f, bool on_device) = 0;
+    virtual Status invariants(double out[6]) = 0;
+    virtual Status gradient(const double *g, double *out, int nfields) = 0;
+    virtual long steps() const = 0;
+    virtual void set_steps(long s) = 0;
+    virtual int launches_per_step() const = 0;
+    virtual const fftlb_params &params() const = 0;
+    // kernel timing: CUDA events around every stage launch, by kernel kind
+    virtual Status profile(int enable) = 0;
+    virtual Status profile_read(double *ms, long *launches, double *bytes, int nkinds) = 0;
+};
+
+// kernel kinds of one stage (index into the profile arrays)
+enum KernelKind {
+    KK_ROW_FORWARD = 0,   // moments + forward row transforms
+    KK_COL_CONV = 1,      // column pass, convection
+    KK_COL_LEVEL1 = 2,    // column pass, level-1 derivatives
+    KK_ROW_LEVEL1 = 3,    // level-1 row inverse + Lambda/Phi + forward rows
+    KK_COL_LEVEL2 = 4,    // column pass, level-2 divergences
+    KK_ROW_FINAL = 5,     // row inverse + force + BGK + RK combination
+    KK_COUNT = 6
+};
+extern const char *const kKernelNames[KK_COUNT];
+
+Engine *make_engine_f64();
+Engine *make_engine_f32();
+
+}  // namespace fftlb

@@ -1,0 +1,1323 @@
+// Templated engine of the FFT-LB method (arXiv:1011.3582): device kernels
+// and the per-precision plan.  Included by engine_f64.cu and engine_f32.cu
+// only (each instantiates one precision).
+//
+// One Runge-Kutta stage L(f) (Eq. 10) runs as six launches on the handle's
+// stream:
+//   K1 row_forward_moments  moments rho, u, T (Eqs. 7-9) of the stage state,
+//                           level-1 fields Pi = P^w - rho T (Eq. 18) and
+//                           g = M/T; forward row transforms of the 32 moving
+//                           f_i and of rho, u_x, u_y, T, Pi, g
+//   K2 col (convection)     column forward -> i (v_x k_m,x + v_y k_m,y) ->
+//                           column inverse for the 32 f_i (in place)
+//   K2 col (level 1)        15 derivative spectra of rho, u, T, Pi, g
+//   K3 row_level1           row inverse of the 15 derivatives; Lambda (Eq. 19),
+//                           Phi = 2 q rho T grad T (Eq. 23), the numerator of
+//                           C (Eq. 22) and of B (Eq. 21); forward row
+//                           transforms of Lambda_xx, Lambda_xy, Lambda_yy,
+//                           Phi_x, Phi_y
+//   K2 col (level 2)        d_b Lambda_xb, d_b Lambda_yb, d_a Phi_a
+//   K5 row_final            row inverse of the convection terms and level-2
+//                           divergences; A, B, C, C_q (Eqs. 20-23), f^eq
+//                           (Eq. 3), I (Eq. 11), BGK and the RK combination.
+//
+// Spectra are stored one-sided: slot s holds [ny][nx/2] complex values of
+// a row-transformed (and later column-transformed) field, with the real
+// row-Nyquist value packed into the imaginary part of column 0.
+#pragma once
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "fft_device.cuh"
+
+namespace fftlb {
+
+constexpr int Q = 33;
+constexpr int NMOV = 32;
+constexpr int NT = 256;          // threads per block of every row / column kernel
+
+// spectrum slots
+constexpr int SLOT_RHO = 32, SLOT_UX = 33, SLOT_UY = 34, SLOT_T = 35, SLOT_PI = 36, SLOT_G = 37;
+constexpr int SLOT_D1 = 38;      // 15 level-1 derivative outputs
+constexpr int ND1 = 15;
+constexpr int SLOT_L2 = 53;      // Lxx, Lxy, Lyy, Phx, Phy; outputs in 53, 55, 56
+constexpr int NSLOT = 58;
+enum { D_RX, D_RY, D_LAP, D_UXX, D_UXY, D_UYX, D_UYY, D_DIVX, D_DIVY, D_TX, D_TY, D_PIX, D_PIY, D_GX, D_GY };
+
+// velocity set (Eq. 1) and weight-polynomial coefficients (Eq. 4); each
+// translation unit holds its own copy
+static __constant__ double c_vx[Q], c_vy[Q], c_v2[Q];
+static __constant__ float c_vxf[Q], c_vyf[Q], c_v2f[Q];
+static __constant__ int c_ring[Q];
+static __constant__ double c_Fk[4][4];    // F_k = T (c3 + T (c2 + T (c1 + T c0)))
+static __constant__ float c_Fkf[4][4];
+
+template <typename real> __device__ __forceinline__ real VX(int i);
+template <> __device__ __forceinline__ double VX<double>(int i) { return c_vx[i]; }
+template <> __device__ __forceinline__ float VX<float>(int i) { return c_vxf[i]; }
+template <typename real> __device__ __forceinline__ real VY(int i);
+template <> __device__ __forceinline__ double VY<double>(int i) { return c_vy[i]; }
+template <> __device__ __forceinline__ float VY<float>(int i) { return c_vyf[i]; }
+template <typename real> __device__ __forceinline__ real V2(int i);
+template <> __device__ __forceinline__ double V2<double>(int i) { return c_v2[i]; }
+template <> __device__ __forceinline__ float V2<float>(int i) { return c_v2f[i]; }
+template <typename real> __device__ __forceinline__ real FKC(int k, int j);
+template <> __device__ __forceinline__ double FKC<double>(int k, int j) { return c_Fk[k][j]; }
+template <> __device__ __forceinline__ float FKC<float>(int k, int j) { return c_Fkf[k][j]; }
+
+template <typename real> struct KP {
+    int nx, ny, h;
+    real dx, dt, tau, a, b, K, H, q, zeta, scale;
+};
+
+// One column-pass group: up to 2 input spectra and 6 outputs; every output
+// is a sum of up to 2 terms M(kx, ky) * input, with
+// M = i (c0 k_x + c1 k_y) + (c2 k_x^2 + c3 k_y^2 + c4 k_x k_y).
+struct GroupDesc {
+    int nin, nout;
+    int in_slot[2];
+    int out_slot[6];
+    int nterm[6];
+    int term_in[6][2];
+    double c[6][2][5];
+};
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+
+template <int DIR, typename C>
+__device__ void fft_rows(C *buf, int n, int nrows, const C *W) {
+    const int maxb = max(1, (16 * NT) / n);
+    for (int r0 = 0; r0 < nrows; r0 += maxb) {
+        block_fft<DIR>(buf + (size_t)r0 * n, n, min(maxb, nrows - r0), W, threadIdx.x, NT);
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_tables(C *dst, const C *src, int n) {
+    for (int i = threadIdx.x; i < n; i += NT) dst[i] = src[i];
+}
+
+// Forward real rows -> packed one-sided spectra, in place in shared memory.
+template <typename C>
+__device__ void rows_r2c(C *buf, int h, int nrows, const C *Wr, const C *Wp) {
+    __syncthreads();
+    fft_rows<-1>(buf, h, nrows, Wr);
+    r2c_post(buf, h, nrows, Wp, threadIdx.x, NT);
+    __syncthreads();
+}
+
+// Packed one-sided spectra -> real rows (unnormalised), in place.
+template <typename C>
+__device__ void rows_c2r(C *buf, int h, int nrows, const C *Wr, const C *Wp) {
+    __syncthreads();
+    c2r_pre(buf, h, nrows, Wp, threadIdx.x, NT);
+    __syncthreads();
+    fft_rows<+1>(buf, h, nrows, Wr);
+}
+
+template <typename real>
+__device__ __forceinline__ void weights_Fk(real T, real F[5]) {
+    real s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        real v = T * (FKC<real>(k, 3) + T * (FKC<real>(k, 2) + T * (FKC<real>(k, 1) + T * FKC<real>(k, 0))));
+        F[k + 1] = v;
+        s += v;
+    }
+    F[0] = real(1) - real(8) * s;
+}
+
+// ---------------------------------------------------------------------------
+// K1: moments + forward row transforms
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(NT) k_row_forward_moments(const real *__restrict__ f,
+                                                            typename cplx_of<real>::type *__restrict__ spec,
+                                                            real *__restrict__ fields,
+                                                            const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                            const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                            KP<real> P, int B) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *buf = Wp + h;
+    real *acc = reinterpret_cast<real *>(buf + (size_t)B * h);   // [4][nx]
+    load_tables(Wr, Wr_g, h);
+    load_tables(Wp, Wp_g, h);
+    const real *frow = f + (size_t)y * nx;
+    for (int x = tid; x < nx; x += NT) {
+        real v = frow[x];   // rest velocity: only the mass moment
+        acc[x] = v;
+        acc[nx + x] = 0;
+        acc[2 * nx + x] = 0;
+        acc[3 * nx + x] = 0;
+    }
+    real *bre = reinterpret_cast<real *>(buf);
+    for (int i0 = 1; i0 < Q; i0 += B) {
+        const int nb = min(B, Q - i0);
+        for (int r = 0; r < nb; ++r) {
+            const int i = i0 + r;
+            const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
+            const real *fi = f + (size_t)i * N + (size_t)y * nx;
+            for (int x = tid; x < nx; x += NT) {
+                real v = fi[x];
+                acc[x] += v;
+                acc[nx + x] += vx * v;
+                acc[2 * nx + x] += vy * v;
+                acc[3 * nx + x] += v2 * v;
+                bre[(size_t)r * nx + x] = v;
+            }
+        }
+        rows_r2c(buf, h, nb, Wr, Wp);
+        for (int r = 0; r < nb; ++r) {
+            C *dst = spec + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
+            for (int k = tid; k < h; k += NT) dst[k] = buf[(size_t)r * h + k];
+        }
+        __syncthreads();
+    }
+    // moments (Eqs. 7-9): rho T = (sum |v|^2 f - rho |u|^2) / 2
+    for (int x = tid; x < nx; x += NT) {
+        real rho = acc[x];
+        real ux = acc[nx + x] / rho, uy = acc[2 * nx + x] / rho;
+        real T = real(0.5) * (acc[3 * nx + x] / rho - (ux * ux + uy * uy));
+        acc[x] = rho;
+        acc[nx + x] = ux;
+        acc[2 * nx + x] = uy;
+        acc[3 * nx + x] = T;
+        fields[(size_t)y * nx + x] = rho;
+        fields[N + (size_t)y * nx + x] = ux;
+        fields[2 * N + (size_t)y * nx + x] = uy;
+        fields[3 * N + (size_t)y * nx + x] = T;
+    }
+    // level-1 fields rho, ux, uy, T, Pi, g
+    for (int j0 = 0; j0 < 6; j0 += B) {
+        const int nb = min(B, 6 - j0);
+        for (int r = 0; r < nb; ++r) {
+            const int j = j0 + r;
+            for (int x = tid; x < nx; x += NT) {
+                real v;
+                if (j < 4) {
+                    v = acc[(size_t)j * nx + x];
+                } else {
+                    real rho = acc[x], T = acc[3 * nx + x];
+                    if (j == 4) v = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;   // Eq. 18
+                    else v = (P.K + P.H * T) / T;                                               // M / T
+                }
+                bre[(size_t)r * nx + x] = v;
+            }
+        }
+        rows_r2c(buf, h, nb, Wr, Wp);
+        for (int r = 0; r < nb; ++r) {
+            C *dst = spec + (size_t)(SLOT_RHO + j0 + r) * slot + (size_t)y * h;
+            for (int k = tid; k < h; k += NT) dst[k] = buf[(size_t)r * h + k];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: column pass  forward -> multiplier -> inverse
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(NT) k_col(typename cplx_of<real>::type *__restrict__ spec,
+                                            const GroupDesc *__restrict__ groups,
+                                            const real *__restrict__ kxt, const real *__restrict__ kyt,
+                                            const typename cplx_of<real>::type *__restrict__ Wc_g, KP<real> P,
+                                            int TW, int nin_max) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ GroupDesc g;
+    const int ny = P.ny, h = P.h, tid = threadIdx.x;
+    const size_t slot = (size_t)ny * h;
+    const int kx0 = blockIdx.x * TW;
+    if (tid == 0) g = groups[blockIdx.y];
+    C *Wc = reinterpret_cast<C *>(smem_raw);
+    C *in = Wc + ny;                                   // [nin_max][TW][ny]
+    C *work = in + (size_t)nin_max * TW * ny;          // [TW][ny]
+    load_tables(Wc, Wc_g, ny);
+    __syncthreads();
+    const int tile = TW * ny;
+    for (int s = 0; s < g.nin; ++s) {
+        const C *src = spec + (size_t)g.in_slot[s] * slot;
+        C *dst = in + (size_t)s * tile;
+        for (int idx = tid; idx < tile; idx += NT) {
+            const int c = idx % TW, yy = idx / TW;
+            dst[c * ny + yy] = src[(size_t)yy * h + kx0 + c];
+        }
+    }
+    __syncthreads();
+    for (int s = 0; s < g.nin; ++s) fft_rows<-1>(in + (size_t)s * tile, ny, TW, Wc);
+    const real scale = P.scale;
+    for (int o = 0; o < g.nout; ++o) {
+        const int nterm = g.nterm[o];
+        real cc[2][5];
+        int tin[2];
+        for (int t = 0; t < 2; ++t) {
+            tin[t] = g.term_in[o][t];
+            for (int e = 0; e < 5; ++e) cc[t][e] = (real)g.c[o][t][e];
+        }
+        for (int idx = tid; idx < tile; idx += NT) {
+            const int c = idx / ny, ky = idx - c * ny;
+            const int kx = kx0 + c;
+            if (kx == 0) continue;
+            const real ax = kxt[kx], ay = kyt[ky];
+            C acc = C{0, 0};
+            for (int t = 0; t < nterm; ++t) {
+                const real mr = cc[t][2] * ax * ax + cc[t][3] * ay * ay + cc[t][4] * ax * ay;
+                const real mi = cc[t][0] * ax + cc[t][1] * ay;
+                const C v = in[(size_t)tin[t] * tile + idx];
+                acc.x += mr * v.x - mi * v.y;
+                acc.y += mr * v.y + mi * v.x;
+            }
+            work[idx] = cscale(acc, scale);
+        }
+        if (kx0 == 0) {
+            // column 0 carries DC (real part) and row-Nyquist (imag part)
+            // columns; separate, multiply each, recombine.
+            const real a0 = kxt[0], aN = kxt[h];
+            for (int j = tid; j <= ny / 2; j += NT) {
+                const int jm = (ny - j) % ny;
+                C outj = C{0, 0}, outm = C{0, 0};
+                for (int t = 0; t < nterm; ++t) {
+                    const C *col = in + (size_t)tin[t] * tile;   // column c = 0
+                    const C p = col[j], q = col[jm];
+                    const C A = cscale(cadd(p, cconj(q)), real(0.5));
+                    const C Bv = cscale(cmul_mi(csub(p, cconj(q))), real(0.5));
+                    const real ay = kyt[j], aym = kyt[jm];
+                    // multiplier at (0, ky) and (Nyquist, ky)
+                    const C M0 = C{cc[t][2] * a0 * a0 + cc[t][3] * ay * ay + cc[t][4] * a0 * ay, cc[t][0] * a0 + cc[t][1] * ay};
+                    const C MN = C{cc[t][2] * aN * aN + cc[t][3] * ay * ay + cc[t][4] * aN * ay, cc[t][0] * aN + cc[t][1] * ay};
+                    const C M0m = C{cc[t][2] * a0 * a0 + cc[t][3] * aym * aym + cc[t][4] * a0 * aym, cc[t][0] * a0 + cc[t][1] * aym};
+                    const C MNm = C{cc[t][2] * aN * aN + cc[t][3] * aym * aym + cc[t][4] * aN * aym, cc[t][0] * aN + cc[t][1] * aym};
+                    outj = cadd(outj, cadd(cmul(M0, A), cmul_i(cmul(MN, Bv))));
+                    outm = cadd(outm, cadd(cmul(M0m, cconj(A)), cmul_i(cmul(MNm, cconj(Bv)))));
+                }
+                work[j] = cscale(outj, scale);
+                if (jm != j) work[jm] = cscale(outm, scale);
+            }
+        }
+        __syncthreads();
+        fft_rows<+1>(work, ny, TW, Wc);
+        C *dst = spec + (size_t)g.out_slot[o] * slot;
+        for (int idx = tid; idx < tile; idx += NT) {
+            const int c = idx % TW, yy = idx / TW;
+            dst[(size_t)yy * h + kx0 + c] = work[c * ny + yy];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: level-1 derivatives -> Lambda, Phi, C and B numerators -> forward rows
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(NT) k_row_level1(typename cplx_of<real>::type *__restrict__ spec,
+                                                   const real *__restrict__ fields, real *__restrict__ aux,
+                                                   const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                   const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                   KP<real> P) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *d = Wp + h;   // [15][h]
+    load_tables(Wr, Wr_g, h);
+    load_tables(Wp, Wp_g, h);
+    for (int o = 0; o < ND1; ++o) {
+        const C *src = spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h;
+        for (int k = tid; k < h; k += NT) d[(size_t)o * h + k] = src[k];
+    }
+    rows_c2r(d, h, ND1, Wr, Wp);
+    __syncthreads();
+    const real *dr = reinterpret_cast<const real *>(d);
+    real *dw = reinterpret_cast<real *>(d);
+    for (int x = tid; x < nx; x += NT) {
+        const size_t s = (size_t)y * nx + x;
+        const real rho = fields[s], T = fields[3 * N + s];
+        const real rx = dr[D_RX * nx + x], ry = dr[D_RY * nx + x], lap = dr[D_LAP * nx + x];
+        const real uxx = dr[D_UXX * nx + x], uxy = dr[D_UXY * nx + x];
+        const real uyx = dr[D_UYX * nx + x], uyy = dr[D_UYY * nx + x];
+        const real divx = dr[D_DIVX * nx + x], divy = dr[D_DIVY * nx + x];
+        const real Tx = dr[D_TX * nx + x], Ty = dr[D_TY * nx + x];
+        const real Pix = dr[D_PIX * nx + x], Piy = dr[D_PIY * nx + x];
+        const real gx = dr[D_GX * nx + x], gy = dr[D_GY * nx + x];
+        const real M = P.K + P.H * T;
+        const real Pi = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;
+        // Eq. 19
+        const real grad2 = rx * rx + ry * ry;
+        const real iso = -(rho * T * (rx * gx + ry * gy)) - M * (rho * lap + real(0.5) * grad2);
+        const real Lxx = M * rx * rx + iso, Lxy = M * rx * ry, Lyy = M * ry * ry + iso;
+        // Eq. 22 numerator (without C_q)
+        const real div = uxx + uyy;
+        const real Ldu = Lxx * uxx + Lxy * (uyx + uxy) + Lyy * uyy;
+        const real Cn = Pi * div + Ldu - P.zeta * div * div + P.a * rho * rho * div +
+                        P.K * (real(-0.5) * grad2 * div - rho * (rx * divx + ry * divy) -
+                               (rx * (uxx * rx + uyx * ry) + ry * (uxy * rx + uyy * ry)));
+        aux[s] = Cn;
+        aux[N + s] = Pix - P.zeta * divx;   // Eq. 21 numerator without d_b Lambda_ab
+        aux[2 * N + s] = Piy - P.zeta * divy;
+        const real q2 = real(2) * P.q * rho * T;   // Eq. 23: Phi = 2 q rho T grad T
+        dw[0 * nx + x] = Lxx;
+        dw[1 * nx + x] = Lxy;
+        dw[2 * nx + x] = Lyy;
+        dw[3 * nx + x] = q2 * Tx;
+        dw[4 * nx + x] = q2 * Ty;
+    }
+    rows_r2c(d, h, 5, Wr, Wp);
+    for (int r = 0; r < 5; ++r) {
+        C *dst = spec + (size_t)(SLOT_L2 + r) * slot + (size_t)y * h;
+        for (int k = tid; k < h; k += NT) dst[k] = d[(size_t)r * h + k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: convection + level-2 -> coefficients -> f^eq, I, BGK, RK combination
+// ---------------------------------------------------------------------------
+
+constexpr int NST = 16;   // per-site state kept in shared memory
+
+template <typename real>
+__global__ void __launch_bounds__(NT) k_row_final(const typename cplx_of<real>::type *__restrict__ spec,
+                                                  const real *__restrict__ fields, const real *__restrict__ aux,
+                                                  const real *fcur, const real *fbase, real *fout, real alpha,
+                                                  real beta, const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                  const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P,
+                                                  int B) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *l2 = Wp + h;                         // [3][h]
+    C *cb = l2 + (size_t)3 * h;              // [B][h]
+    real *st = reinterpret_cast<real *>(cb + (size_t)B * h);   // [NST][nx]
+    load_tables(Wr, Wr_g, h);
+    load_tables(Wp, Wp_g, h);
+    const int l2slots[3] = {SLOT_L2 + 0, SLOT_L2 + 2, SLOT_L2 + 3};
+    for (int r = 0; r < 3; ++r) {
+        const C *src = spec + (size_t)l2slots[r] * slot + (size_t)y * h;
+        for (int k = tid; k < h; k += NT) l2[(size_t)r * h + k] = src[k];
+    }
+    rows_c2r(l2, h, 3, Wr, Wp);
+    const real *l2r = reinterpret_cast<const real *>(l2);
+    for (int x = tid; x < nx; x += NT) {
+        const size_t s = (size_t)y * nx + x;
+        const real rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
+        const real rT = rho * T;
+        const real inv2 = real(1) / (real(2) * rho * T * T);
+        const real Bx = (aux[N + s] + l2r[x]) / rT;            // Eq. 21
+        const real By = (aux[2 * N + s] + l2r[nx + x]) / rT;
+        const real Cc = aux[s] * inv2;                           // Eq. 22
+        const real Cq = l2r[2 * nx + x] * inv2;                  // Eq. 23
+        const real CC = Cc + Cq;
+        const real A = real(-2) * CC * T;                        // Eq. 20
+        const real u2 = ux * ux + uy * uy;
+        real F[5];
+        weights_Fk<real>(T, F);                                  // Eqs. 4-6
+        const real iT = real(1) / T;
+        const real qq = real(0.5) * u2 * iT;                     // u^2 / 2T
+        const real om = real(1) - qq;
+        st[0 * nx + x] = rho * F[0];
+        st[1 * nx + x] = rho * F[1];
+        st[2 * nx + x] = rho * F[2];
+        st[3 * nx + x] = rho * F[3];
+        st[4 * nx + x] = rho * F[4];
+        st[5 * nx + x] = om + real(0.5) * qq * qq;               // 1 - u^2/2T + u^4/8T^2
+        st[6 * nx + x] = om * iT;
+        st[7 * nx + x] = real(0.5) * om * iT * iT;
+        st[8 * nx + x] = iT * iT * iT / real(6);
+        st[9 * nx + x] = iT * iT * iT * iT / real(24);
+        st[10 * nx + x] = ux;
+        st[11 * nx + x] = uy;
+        // I = -(A + B.(v-u) + CC |v-u|^2) f^eq = -(e0 + e1.v + CC |v|^2) f^eq
+        st[12 * nx + x] = A - (Bx * ux + By * uy) + CC * u2;
+        st[13 * nx + x] = Bx - real(2) * CC * ux;
+        st[14 * nx + x] = By - real(2) * CC * uy;
+        st[15 * nx + x] = CC;
+    }
+    __syncthreads();
+    const real dt = P.dt, itau = real(1) / P.tau;
+    const real *cr = reinterpret_cast<const real *>(cb);
+    // rest velocity (no convection)
+    for (int x = tid; x < nx; x += NT) {
+        const size_t s = (size_t)y * nx + x;
+        const real fe = st[0 * nx + x] * st[5 * nx + x];
+        const real I = -st[12 * nx + x] * fe;
+        const real fc = fcur[s];
+        const real rhs = -(fc - fe) * itau + I;
+        real fn = beta * (fc + dt * rhs);
+        if (alpha != real(0)) fn += alpha * fbase[s];
+        fout[s] = fn;
+    }
+    for (int i0 = 1; i0 < Q; i0 += B) {
+        const int nb = min(B, Q - i0);
+        for (int r = 0; r < nb; ++r) {
+            const C *src = spec + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
+            for (int k = tid; k < h; k += NT) cb[(size_t)r * h + k] = src[k];
+        }
+        rows_c2r(cb, h, nb, Wr, Wp);
+        for (int x = tid; x < nx; x += NT) {
+            real sv[NST];
+#pragma unroll
+            for (int e = 0; e < NST; ++e) sv[e] = st[e * nx + x];
+            for (int r = 0; r < nb; ++r) {
+                const int i = i0 + r;
+                const size_t s = (size_t)i * N + (size_t)y * nx + x;
+                const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
+                const int k = c_ring[i];
+                const real vu = vx * sv[10] + vy * sv[11];
+                const real br = sv[5] + vu * (sv[6] + vu * (sv[7] + vu * (sv[8] + vu * sv[9])));
+                real rF = sv[0];
+                rF = (k == 1) ? sv[1] : rF;
+                rF = (k == 2) ? sv[2] : rF;
+                rF = (k == 3) ? sv[3] : rF;
+                rF = (k == 4) ? sv[4] : rF;
+                const real fe = rF * br;                                   // Eq. 3
+                const real I = -(sv[12] + sv[13] * vx + sv[14] * vy + sv[15] * v2) * fe;   // Eq. 11
+                const real fc = fcur[s];
+                const real conv = cr[(size_t)r * nx + x];
+                const real rhs = -conv - (fc - fe) * itau + I;             // Eq. 10
+                real fn = beta * (fc + dt * rhs);
+                if (alpha != real(0)) fn += alpha * fbase[s];
+                fout[s] = fn;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// auxiliary kernels: equilibrium init, moments, generic transforms, sums
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void k_feq_init(const double *rho_g, const double *ux_g, const double *uy_g, const double *T_g,
+                           real *f, size_t N) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < N; s += (size_t)gridDim.x * blockDim.x) {
+        const real rho = (real)rho_g[s], ux = (real)ux_g[s], uy = (real)uy_g[s], T = (real)T_g[s];
+        real F[5];
+        weights_Fk<real>(T, F);
+        const real u2 = ux * ux + uy * uy, iT = real(1) / T, qq = real(0.5) * u2 * iT, om = real(1) - qq;
+        const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
+        const real p3 = iT * iT * iT / real(6), p4 = iT * iT * iT * iT / real(24);
+        for (int i = 0; i < Q; ++i) {
+            const real vu = VX<real>(i) * ux + VY<real>(i) * uy;
+            f[(size_t)i * N + s] = rho * F[c_ring[i]] * (p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4))));
+        }
+    }
+}
+
+template <typename real>
+__global__ void k_moments(const real *f, real *fields, size_t N) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < N; s += (size_t)gridDim.x * blockDim.x) {
+        real m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        for (int i = 0; i < Q; ++i) {
+            const real v = f[(size_t)i * N + s];
+            m0 += v;
+            m1 += VX<real>(i) * v;
+            m2 += VY<real>(i) * v;
+            m3 += V2<real>(i) * v;
+        }
+        const real ux = m1 / m0, uy = m2 / m0;
+        fields[s] = m0;
+        fields[N + s] = ux;
+        fields[2 * N + s] = uy;
+        fields[3 * N + s] = real(0.5) * (m3 / m0 - (ux * ux + uy * uy));
+    }
+}
+
+template <typename real, typename TO>
+__global__ void k_convert(const real *src, TO *dst, size_t n) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x)
+        dst[s] = (TO)src[s];
+}
+
+// Forward row transforms of nf real fields (row-major [nf][ny][nx]) into
+// spectrum slots slot0 .. slot0 + nf - 1.  grid = (ny, nf).
+template <typename real, typename TIn>
+__global__ void __launch_bounds__(NT) k_rows_forward(const TIn *__restrict__ in, typename cplx_of<real>::type *spec,
+                                                     int slot0, const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                     const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, fi = blockIdx.y, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *buf = Wp + h;
+    load_tables(Wr, Wr_g, h);
+    load_tables(Wp, Wp_g, h);
+    real *bre = reinterpret_cast<real *>(buf);
+    for (int x = tid; x < nx; x += NT) bre[x] = (real)in[(size_t)fi * N + (size_t)y * nx + x];
+    rows_r2c(buf, h, 1, Wr, Wp);
+    C *dst = spec + (size_t)(slot0 + fi) * slot + (size_t)y * h;
+    for (int k = tid; k < h; k += NT) dst[k] = buf[k];
+}
+
+// Inverse row transforms of nf spectrum slots into real fields.  grid = (ny, nf).
+template <typename real, typename TOut>
+__global__ void __launch_bounds__(NT) k_rows_inverse(const typename cplx_of<real>::type *spec, int slot0,
+                                                     TOut *__restrict__ out,
+                                                     const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                     const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, fi = blockIdx.y, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *buf = Wp + h;
+    load_tables(Wr, Wr_g, h);
+    load_tables(Wp, Wp_g, h);
+    const C *src = spec + (size_t)(slot0 + fi) * slot + (size_t)y * h;
+    for (int k = tid; k < h; k += NT) buf[k] = src[k];
+    rows_c2r(buf, h, 1, Wr, Wp);
+    __syncthreads();
+    const real *bre = reinterpret_cast<const real *>(buf);
+    for (int x = tid; x < nx; x += NT) out[(size_t)fi * N + (size_t)y * nx + x] = (TOut)bre[x];
+}
+
+// Per-row fp64 partial sums for the invariants: mass, momentum, e_T
+// (Eq. 17, grad rho from spectrum slots 1 and 2), max |u|, and a count of
+// non-finite or unphysical sites.  grid = ny.
+template <typename real>
+__global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<real>::type *spec,
+                                                       const real *__restrict__ fields, double *partial,
+                                                       const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                       const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                       KP<real> P, int with_grad) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[6][NT];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *buf = Wp + h;   // [2][h]
+    if (with_grad) {
+        load_tables(Wr, Wr_g, h);
+        load_tables(Wp, Wp_g, h);
+        for (int r = 0; r < 2; ++r) {
+            const C *src = spec + (size_t)(1 + r) * slot + (size_t)y * h;
+            for (int k = tid; k < h; k += NT) buf[(size_t)r * h + k] = src[k];
+        }
+        rows_c2r(buf, h, 2, Wr, Wp);
+        __syncthreads();
+    }
+    const real *g = reinterpret_cast<const real *>(buf);
+    double m = 0, px = 0, py = 0, e = 0, um = 0, bad = 0;
+    for (int x = tid; x < nx; x += NT) {
+        const size_t s = (size_t)y * nx + x;
+        const double rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
+        double g2 = 0;
+        if (with_grad) {
+            const double rx = g[x], ry = g[nx + x];
+            g2 = rx * rx + ry * ry;
+        }
+        const double u2 = ux * ux + uy * uy;
+        m += rho;
+        px += rho * ux;
+        py += rho * uy;
+        e += rho * T - (double)P.a * rho * rho + (double)P.K * g2 * 0.5 + rho * u2 * 0.5;
+        um = fmax(um, sqrt(u2));
+        const bool ok = isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(T) && rho > 0 && T > 0 &&
+                        (double)P.b * rho < 1.0;
+        bad += ok ? 0.0 : 1.0;
+    }
+    red[0][tid] = m;
+    red[1][tid] = px;
+    red[2][tid] = py;
+    red[3][tid] = e;
+    red[4][tid] = um;
+    red[5][tid] = bad;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+            for (int q = 0; q < 6; ++q) {
+                if (q == 4) red[q][tid] = fmax(red[q][tid], red[q][tid + w]);
+                else red[q][tid] += red[q][tid + w];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < 6) partial[(size_t)y * 6 + tid] = red[tid][0];
+}
+
+static __global__ void k_reduce_partials(const double *partial, int ny, double *out) {
+    __shared__ double red[6][NT];
+    const int tid = threadIdx.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int y = tid; y < ny; y += NT) {
+        for (int q = 0; q < 6; ++q) {
+            const double v = partial[(size_t)y * 6 + q];
+            acc[q] = (q == 4) ? fmax(acc[q], v) : acc[q] + v;
+        }
+    }
+    for (int q = 0; q < 6; ++q) red[q][tid] = acc[q];
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (tid < w)
+            for (int q = 0; q < 6; ++q)
+                red[q][tid] = (q == 4) ? fmax(red[q][tid], red[q][tid + w]) : red[q][tid] + red[q][tid + w];
+        __syncthreads();
+    }
+    if (tid < 6) out[tid] = red[tid][0];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+#define FFTLB_CU(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return Status::err(e_ == cudaErrorMemoryAllocation ? FFTLB_ERR_OOM : FFTLB_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+#define FFTLB_LAUNCHED(name)                                                                 \
+    do {                                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                                 \
+        if (e_ != cudaSuccess)                                                               \
+            return Status::err(FFTLB_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static inline bool valid_len(int n) {
+    if (n < 4 || (n & 1)) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+template <typename real>
+class EngineT : public Engine {
+    using C = typename cplx_of<real>::type;
+
+  public:
+    ~EngineT() override {
+        for (auto &e : prof_pool_) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+        release();
+    }
+
+    Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s) override {
+        p_ = p;
+        stream_ = s;
+        const int maxn = sizeof(real) == 8 ? 1024 : 2048;
+        if (!valid_len(p.nx) || !valid_len(p.ny) || p.nx > maxn || p.ny > maxn)
+            return Status::err(FFTLB_ERR_ARG, "nx, ny must be even 2^p 3^q in [4, " + std::to_string(maxn) + "]");
+        if (!(p.tau > 0) || !(p.dx > 0) || !(p.dt > 0)) return Status::err(FFTLB_ERR_ARG, "tau, dx, dt must be > 0");
+        if (p.window < 0 || p.window > 4) return Status::err(FFTLB_ERR_ARG, "window must be 0..4");
+        if (p.integrator != 1 && p.integrator != 3) return Status::err(FFTLB_ERR_ARG, "integrator must be 1 or 3");
+        if (!(p.b >= 0) || !(p.a >= 0)) return Status::err(FFTLB_ERR_ARG, "a, b must be >= 0");
+        nx_ = p.nx;
+        ny_ = p.ny;
+        h_ = nx_ / 2;
+        N_ = (size_t)nx_ * ny_;
+        Status st = upload_constants(speeds);
+        if (!st.good()) return st;
+        st = alloc();
+        if (!st.good()) return st;
+        st = build_tables();
+        if (!st.good()) return st;
+        st = build_groups();
+        if (!st.good()) return st;
+        return configure();
+    }
+
+    Status set_fields(const double *rho, const double *ux, const double *uy, const double *T, bool on_device) override {
+        const double *src[4] = {rho, ux, uy, T};
+        for (int i = 0; i < 4; ++i)
+            if (!src[i]) return Status::err(FFTLB_ERR_ARG, "set_fields: NULL field");
+        double *tmp = reinterpret_cast<double *>(scratch_d_);
+        for (int i = 0; i < 4; ++i)
+            FFTLB_CU(cudaMemcpyAsync(tmp + i * N_, src[i], N_ * sizeof(double),
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream_));
+        k_feq_init<real><<<grid1d(), 256, 0, stream_>>>(tmp, tmp + N_, tmp + 2 * N_, tmp + 3 * N_, f0_, N_);
+        FFTLB_LAUNCHED("k_feq_init");
+        FFTLB_CU(cudaStreamSynchronize(stream_));
+        steps_ = 0;
+        return Status::ok();
+    }
+
+    Status step(long nsteps, long *done) override {
+        if (done) *done = 0;
+        if (nsteps < 0) return Status::err(FFTLB_ERR_ARG, "nsteps < 0");
+        for (long n = 0; n < nsteps; ++n) {
+            Status st;
+            if (p_.integrator == 1) {
+                st = stage(f0_, nullptr, f0_, real(0), real(1));
+            } else {
+                st = stage(f0_, nullptr, f1_, real(0), real(1));
+                if (st.good()) st = stage(f1_, f0_, f1_, real(0.75), real(0.25));
+                if (st.good()) st = stage(f1_, f0_, f0_, real(1.0 / 3.0), real(2.0 / 3.0));
+            }
+            if (!st.good()) return st;
+            ++steps_;
+            if (done) *done = n + 1;
+            if (p_.check_every > 0 && (steps_ % p_.check_every) == 0) {
+                double inv[6];
+                st = sums(false, inv);
+                if (!st.good()) return st;
+                if (inv[5] > 0)
+                    return Status::err(FFTLB_ERR_UNSTABLE, "non-finite or unphysical state after step " +
+                                                               std::to_string(steps_));
+            }
+        }
+        return Status::ok();
+    }
+
+    Status fields(double *rho, double *ux, double *uy, double *T, bool on_device) override {
+        k_moments<real><<<grid1d(), 256, 0, stream_>>>(f0_, fields_, N_);
+        FFTLB_LAUNCHED("k_moments");
+        double *tmp = reinterpret_cast<double *>(scratch_d_);
+        k_convert<real, double><<<grid1d(), 256, 0, stream_>>>(fields_, tmp, 4 * N_);
+        FFTLB_LAUNCHED("k_convert");
+        double *dst[4] = {rho, ux, uy, T};
+        for (int i = 0; i < 4; ++i) {
+            if (!dst[i]) continue;
+            FFTLB_CU(cudaMemcpyAsync(dst[i], tmp + i * N_, N_ * sizeof(double),
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream_));
+        }
+        if (!on_device) FFTLB_CU(cudaStreamSynchronize(stream_));
+        return Status::ok();
+    }
+
+    Status get_f(double *f, bool on_device) override {
+        if (!f) return Status::err(FFTLB_ERR_ARG, "get_f: NULL");
+        if (sizeof(real) == 8 && on_device) {
+            FFTLB_CU(cudaMemcpyAsync(f, f0_, Q * N_ * sizeof(double), cudaMemcpyDeviceToDevice, stream_));
+            return Status::ok();
+        }
+        double *tmp = reinterpret_cast<double *>(scratch_d_);   // scratch holds >= 33 N doubles
+        k_convert<real, double><<<grid1d(), 256, 0, stream_>>>(f0_, tmp, Q * N_);
+        FFTLB_LAUNCHED("k_convert");
+        FFTLB_CU(cudaMemcpyAsync(f, tmp, Q * N_ * sizeof(double),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream_));
+        if (!on_device) FFTLB_CU(cudaStreamSynchronize(stream_));
+        return Status::ok();
+    }
+
+    Status set_f(const double *f, bool on_device) override {
+        if (!f) return Status::err(FFTLB_ERR_ARG, "set_f: NULL");
+        double *tmp = reinterpret_cast<double *>(scratch_d_);
+        FFTLB_CU(cudaMemcpyAsync(tmp, f, Q * N_ * sizeof(double),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream_));
+        k_convert<double, real><<<grid1d(), 256, 0, stream_>>>(tmp, f0_, Q * N_);
+        FFTLB_LAUNCHED("k_convert");
+        FFTLB_CU(cudaStreamSynchronize(stream_));
+        return Status::ok();
+    }
+
+    Status invariants(double out[6]) override {
+        double inv[6];
+        Status st = sums(true, inv);
+        if (!st.good()) return st;
+        const double area = p_.dx * p_.dx;
+        out[0] = inv[0] * area;
+        out[1] = inv[1] * area;
+        out[2] = inv[2] * area;
+        out[3] = inv[3] * area;
+        out[4] = inv[4];
+        out[5] = steps_ * p_.dt;
+        return Status::ok();
+    }
+
+    Status gradient(const double *g, double *out, int nfields) override {
+        if (!g || !out || nfields < 1 || nfields > 16)
+            return Status::err(FFTLB_ERR_ARG, "gradient: need device pointers and 1 <= nfields <= 16");
+        k_rows_forward<real, double><<<dim3(ny_, nfields), NT, smem_rows1_, stream_>>>(g, spec_, 0, Wr_, Wp_, kp_);
+        FFTLB_LAUNCHED("k_rows_forward");
+        Status st = run_groups(grad_groups_ + 0, nfields, 1);
+        if (!st.good()) return st;
+        k_rows_inverse<real, double><<<dim3(ny_, 2 * nfields), NT, smem_rows1_, stream_>>>(spec_, 20, out, Wr_, Wp_, kp_);
+        FFTLB_LAUNCHED("k_rows_inverse");
+        return Status::ok();
+    }
+
+    long steps() const override { return steps_; }
+    void set_steps(long s) override { steps_ = s; }
+    int launches_per_step() const override { return 6 * (p_.integrator == 1 ? 1 : 3); }
+    const fftlb_params &params() const override { return p_; }
+
+  private:
+    fftlb_params p_{};
+    cudaStream_t stream_ = nullptr;
+    int nx_ = 0, ny_ = 0, h_ = 0;
+    size_t N_ = 0;
+    long steps_ = 0;
+    KP<real> kp_{};
+    // device memory
+    real *f0_ = nullptr, *f1_ = nullptr, *fields_ = nullptr, *aux_ = nullptr;
+    C *spec_ = nullptr;
+    real *kxt_ = nullptr, *kyt_ = nullptr;
+    C *Wr_ = nullptr, *Wp_ = nullptr, *Wc_ = nullptr;
+    GroupDesc *groups_ = nullptr;
+    double *partial_ = nullptr, *red_ = nullptr;
+    void *scratch_d_ = nullptr;
+    std::vector<void *> allocs_;
+    // group ranges in groups_
+    int conv_groups_ = 0, l1_groups_ = 0, l2_groups_ = 0, grad_groups_ = 0, inv_groups_ = 0;
+    // launch configuration
+    int TW_ = 1;
+    size_t smem_k1_ = 0, smem_k3_ = 0, smem_k5_ = 0, smem_col1_ = 0, smem_col2_ = 0, smem_rows1_ = 0, smem_inv_ = 0;
+    int B1_ = 1, B5_ = 1;
+    // profiling
+    bool prof_ = false;
+    struct ProfEv {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfEv> prof_pool_;
+    size_t prof_used_ = 0;
+    double prof_ms_[KK_COUNT] = {0};
+    long prof_n_[KK_COUNT] = {0};
+    int prof_kind_ = 0;
+
+    Status prof_begin(int kind) {
+        if (!prof_) return Status::ok();
+        if (prof_used_ == prof_pool_.size()) {
+            ProfEv e;
+            e.kind = kind;
+            FFTLB_CU(cudaEventCreate(&e.a));
+            FFTLB_CU(cudaEventCreate(&e.b));
+            prof_pool_.push_back(e);
+        }
+        prof_pool_[prof_used_].kind = kind;
+        FFTLB_CU(cudaEventRecord(prof_pool_[prof_used_].a, stream_));
+        return Status::ok();
+    }
+    Status prof_end() {
+        if (!prof_) return Status::ok();
+        FFTLB_CU(cudaEventRecord(prof_pool_[prof_used_].b, stream_));
+        ++prof_used_;
+        if (prof_used_ >= 4096) return prof_flush();
+        return Status::ok();
+    }
+    Status prof_flush() {
+        if (prof_used_ == 0) return Status::ok();
+        FFTLB_CU(cudaEventSynchronize(prof_pool_[prof_used_ - 1].b));
+        for (size_t i = 0; i < prof_used_; ++i) {
+            float ms = 0;
+            FFTLB_CU(cudaEventElapsedTime(&ms, prof_pool_[i].a, prof_pool_[i].b));
+            prof_ms_[prof_pool_[i].kind] += ms;
+            prof_n_[prof_pool_[i].kind] += 1;
+        }
+        prof_used_ = 0;
+        return Status::ok();
+    }
+
+  public:
+    Status profile(int enable) override {
+        Status st = prof_flush();
+        if (!st.good()) return st;
+        prof_ = enable != 0;
+        for (int k = 0; k < KK_COUNT; ++k) {
+            prof_ms_[k] = 0;
+            prof_n_[k] = 0;
+        }
+        return Status::ok();
+    }
+    Status profile_read(double *ms, long *launches, double *bytes, int nkinds) override {
+        Status st = prof_flush();
+        if (!st.good()) return st;
+        const double s = sizeof(real), NN = (double)N_;
+        const double fbase = p_.integrator == 3 ? 2.0 / 3.0 : 0.0;   // stages 2, 3 read f^n
+        // algorithmic bytes per launch: every value each kernel must read or
+        // write once (one-sided spectra count N reals per field)
+        const double alg[KK_COUNT] = {
+            (33 + 38 + 4) * NN * s,                   // f in; 38 spectra + rho, u, T out
+            (32 + 32) * NN * s,                       // 32 spectra in, 32 out
+            (6 + 15) * NN * s,                        // 6 in, 15 out
+            (15 + 2 + 3 + 5) * NN * s,                // 15 + rho, T in; 3 aux + 5 spectra out
+            (5 + 3) * NN * s,                         // 5 in, 3 out
+            (32 + 3 + 4 + 3 + 33 + 33 * fbase + 33) * NN * s};
+        for (int k = 0; k < nkinds && k < KK_COUNT; ++k) {
+            if (ms) ms[k] = prof_ms_[k];
+            if (launches) launches[k] = prof_n_[k];
+            if (bytes) bytes[k] = alg[k];
+        }
+        return Status::ok();
+    }
+
+  private:
+
+    unsigned grid1d() const {
+        size_t b = (N_ + 255) / 256;
+        return (unsigned)(b > 4096 ? 4096 : b);
+    }
+
+    template <typename T> Status dalloc(T **ptr, size_t count) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return Status::err(FFTLB_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+        }
+        allocs_.push_back(p);
+        *ptr = reinterpret_cast<T *>(p);
+        return Status::ok();
+    }
+
+    void release() {
+        for (void *p : allocs_) cudaFree(p);
+        allocs_.clear();
+    }
+
+    Status upload_constants(const double speeds[4]) {
+        double vx[Q], vy[Q], v2[Q];
+        float vxf[Q], vyf[Q], v2f[Q];
+        int ring[Q];
+        vx[0] = vy[0] = v2[0] = 0;
+        ring[0] = 0;
+        const long double pi = 3.141592653589793238462643383279502884L;
+        for (int k = 0; k < 4; ++k)
+            for (int i = 0; i < 8; ++i) {
+                const int j = 1 + 8 * k + i;
+                // exact cos/sin of multiples of pi/4
+                static const long double cs[8] = {1.0L, 0.707106781186547524400844362104849039L, 0.0L,
+                                                  -0.707106781186547524400844362104849039L, -1.0L,
+                                                  -0.707106781186547524400844362104849039L, 0.0L,
+                                                  0.707106781186547524400844362104849039L};
+                const long double c = cs[i], s = cs[(i + 6) % 8];
+                (void)pi;
+                vx[j] = (double)(speeds[k] * c);
+                vy[j] = (double)(speeds[k] * s);
+                v2[j] = vx[j] * vx[j] + vy[j] * vy[j];
+                ring[j] = k + 1;
+            }
+        for (int j = 0; j < Q; ++j) {
+            vxf[j] = (float)vx[j];
+            vyf[j] = (float)vy[j];
+            v2f[j] = (float)v2[j];
+        }
+        // Eq. 4: F_k = [48 T^4 - 6 s1 T^3 + s2 T^2 - s3 T / 4] / [v_k^2 prod_l (v_k^2 - o_l)],
+        // o_l = v_{k+l}^2 with the cyclic index of Eq. 6
+        double Fk[4][4];
+        float Fkf[4][4];
+        for (int k = 0; k < 4; ++k) {
+            double o[3];
+            for (int l = 1; l <= 3; ++l) o[l - 1] = speeds[(k + l) % 4] * speeds[(k + l) % 4];
+            const double vk2 = speeds[k] * speeds[k];
+            const double den = vk2 * (vk2 - o[0]) * (vk2 - o[1]) * (vk2 - o[2]);
+            if (den == 0) return Status::err(FFTLB_ERR_ARG, "velocity set: speeds must be distinct and non-zero");
+            Fk[k][0] = 48.0 / den;
+            Fk[k][1] = -6.0 * (o[0] + o[1] + o[2]) / den;
+            Fk[k][2] = (o[0] * o[1] + o[1] * o[2] + o[2] * o[0]) / den;
+            Fk[k][3] = -o[0] * o[1] * o[2] / (4.0 * den);
+            for (int j = 0; j < 4; ++j) Fkf[k][j] = (float)Fk[k][j];
+        }
+        FFTLB_CU(cudaMemcpyToSymbol(c_vx, vx, sizeof vx));
+        FFTLB_CU(cudaMemcpyToSymbol(c_vy, vy, sizeof vy));
+        FFTLB_CU(cudaMemcpyToSymbol(c_v2, v2, sizeof v2));
+        FFTLB_CU(cudaMemcpyToSymbol(c_vxf, vxf, sizeof vxf));
+        FFTLB_CU(cudaMemcpyToSymbol(c_vyf, vyf, sizeof vyf));
+        FFTLB_CU(cudaMemcpyToSymbol(c_v2f, v2f, sizeof v2f));
+        FFTLB_CU(cudaMemcpyToSymbol(c_ring, ring, sizeof ring));
+        FFTLB_CU(cudaMemcpyToSymbol(c_Fk, Fk, sizeof Fk));
+        FFTLB_CU(cudaMemcpyToSymbol(c_Fkf, Fkf, sizeof Fkf));
+        memcpy(vx_, vx, sizeof vx);
+        memcpy(vy_, vy, sizeof vy);
+        return Status::ok();
+    }
+    double vx_[Q], vy_[Q];
+
+    Status alloc() {
+        Status st;
+        if (!(st = dalloc(&f0_, Q * N_)).good()) return st;
+        if (p_.integrator == 3 && !(st = dalloc(&f1_, Q * N_)).good()) return st;
+        if (!(st = dalloc(&spec_, (size_t)NSLOT * ny_ * h_)).good()) return st;
+        if (!(st = dalloc(&fields_, 4 * N_)).good()) return st;
+        if (!(st = dalloc(&aux_, 3 * N_)).good()) return st;
+        if (!(st = dalloc(&kxt_, (size_t)h_ + 1)).good()) return st;
+        if (!(st = dalloc(&kyt_, (size_t)ny_)).good()) return st;
+        if (!(st = dalloc(&Wr_, (size_t)h_)).good()) return st;
+        if (!(st = dalloc(&Wp_, (size_t)h_)).good()) return st;
+        if (!(st = dalloc(&Wc_, (size_t)ny_)).good()) return st;
+        if (!(st = dalloc(&partial_, (size_t)ny_ * 6)).good()) return st;
+        if (!(st = dalloc(&red_, 8)).good()) return st;
+        // fp64 staging for conversions: 33 N doubles (reuses nothing else)
+        double *sc = nullptr;
+        if (!(st = dalloc(&sc, Q * N_)).good()) return st;
+        scratch_d_ = sc;
+        return Status::ok();
+    }
+
+    // windowed wavenumber (Eqs. K1-K4) for bin index n in [-N/2, N/2 - 1];
+    // the Nyquist bin is zeroed (the real part of the paper's inverse
+    // transform of i k f~ receives nothing from it)
+    long double kappa(int n, int Nlen) const {
+        if (2 * n == -Nlen || 2 * n == Nlen) return 0.0L;
+        const long double pi = 3.141592653589793238462643383279502884L;
+        const long double dx = p_.dx;
+        const long double k = 2.0L * pi * n / (Nlen * dx);
+        if (p_.window == 0) return k;
+        const long double s = sinl(pi * n / Nlen);
+        // arcsin series coefficients (2j)! / (4^j (j!)^2 (2j+1))
+        long double sum = 0, c = 1.0L, sp = s;
+        for (int j = 0; j < p_.window; ++j) {
+            if (j > 0) c = c * (2.0L * j - 1.0L) * (2.0L * j - 1.0L) / ((2.0L * j) * (2.0L * j + 1.0L));
+            sum += c * sp;
+            sp *= s * s;
+        }
+        return sum * 2.0L / dx;
+    }
+
+    static void twiddles(std::vector<C> &w, int n, int len) {
+        // w[m] = exp(-2 pi i m / n), m < len
+        const long double pi = 3.141592653589793238462643383279502884L;
+        w.resize(len);
+        for (int m = 0; m < len; ++m) {
+            const long double a = 2.0L * pi * (long double)m / (long double)n;
+            w[m].x = (real)cosl(a);
+            w[m].y = (real)(-sinl(a));
+        }
+    }
+
+    Status build_tables() {
+        std::vector<real> kx(h_ + 1), ky(ny_);
+        for (int j = 0; j <= h_; ++j) kx[j] = (real)kappa(j, nx_);   // j = h is the Nyquist bin
+        for (int j = 0; j < ny_; ++j) ky[j] = (real)kappa(j < ny_ / 2 ? j : j - ny_, ny_);
+        std::vector<C> wr, wp, wc;
+        twiddles(wr, h_, h_);
+        twiddles(wp, nx_, h_);
+        twiddles(wc, ny_, ny_);
+        FFTLB_CU(cudaMemcpy(kxt_, kx.data(), kx.size() * sizeof(real), cudaMemcpyHostToDevice));
+        FFTLB_CU(cudaMemcpy(kyt_, ky.data(), ky.size() * sizeof(real), cudaMemcpyHostToDevice));
+        FFTLB_CU(cudaMemcpy(Wr_, wr.data(), wr.size() * sizeof(C), cudaMemcpyHostToDevice));
+        FFTLB_CU(cudaMemcpy(Wp_, wp.data(), wp.size() * sizeof(C), cudaMemcpyHostToDevice));
+        FFTLB_CU(cudaMemcpy(Wc_, wc.data(), wc.size() * sizeof(C), cudaMemcpyHostToDevice));
+        return Status::ok();
+    }
+
+    static GroupDesc group(int nin, int in0, int in1) {
+        GroupDesc g;
+        memset(&g, 0, sizeof g);
+        g.nin = nin;
+        g.in_slot[0] = in0;
+        g.in_slot[1] = in1;
+        return g;
+    }
+    // add output: term list of (input index, c0..c4)
+    static void add_out(GroupDesc &g, int out_slot, int nterm, int t0, const double c0[5], int t1 = 0,
+                        const double *c1 = nullptr) {
+        const int o = g.nout++;
+        g.out_slot[o] = out_slot;
+        g.nterm[o] = nterm;
+        g.term_in[o][0] = t0;
+        g.term_in[o][1] = t1;
+        for (int e = 0; e < 5; ++e) {
+            g.c[o][0][e] = c0[e];
+            g.c[o][1][e] = c1 ? c1[e] : 0.0;
+        }
+    }
+
+    Status build_groups() {
+        static const double DX[5] = {1, 0, 0, 0, 0}, DY[5] = {0, 1, 0, 0, 0};
+        static const double DXX[5] = {0, 0, -1, 0, 0}, DYY[5] = {0, 0, 0, -1, 0}, DXY[5] = {0, 0, 0, 0, -1};
+        static const double LAP[5] = {0, 0, -1, -1, 0};
+        std::vector<GroupDesc> gs;
+        // convection: i (v_x k_x + v_y k_y) f_i, in place
+        conv_groups_ = (int)gs.size();
+        for (int i = 1; i < Q; ++i) {
+            GroupDesc g = group(1, i - 1, 0);
+            const double c[5] = {vx_[i], vy_[i], 0, 0, 0};
+            add_out(g, i - 1, 1, 0, c);
+            gs.push_back(g);
+        }
+        // level 1
+        l1_groups_ = (int)gs.size();
+        {
+            GroupDesc g = group(1, SLOT_RHO, 0);
+            add_out(g, SLOT_D1 + D_RX, 1, 0, DX);
+            add_out(g, SLOT_D1 + D_RY, 1, 0, DY);
+            add_out(g, SLOT_D1 + D_LAP, 1, 0, LAP);
+            gs.push_back(g);
+        }
+        {
+            GroupDesc g = group(2, SLOT_UX, SLOT_UY);
+            add_out(g, SLOT_D1 + D_UXX, 1, 0, DX);
+            add_out(g, SLOT_D1 + D_UXY, 1, 0, DY);
+            add_out(g, SLOT_D1 + D_UYX, 1, 1, DX);
+            add_out(g, SLOT_D1 + D_UYY, 1, 1, DY);
+            add_out(g, SLOT_D1 + D_DIVX, 2, 0, DXX, 1, DXY);   // D_x (D_x u_x + D_y u_y)
+            add_out(g, SLOT_D1 + D_DIVY, 2, 0, DXY, 1, DYY);   // D_y (D_x u_x + D_y u_y)
+            gs.push_back(g);
+        }
+        const int singles[3][3] = {{SLOT_T, D_TX, D_TY}, {SLOT_PI, D_PIX, D_PIY}, {SLOT_G, D_GX, D_GY}};
+        for (auto &sgl : singles) {
+            GroupDesc g = group(1, sgl[0], 0);
+            add_out(g, SLOT_D1 + sgl[1], 1, 0, DX);
+            add_out(g, SLOT_D1 + sgl[2], 1, 0, DY);
+            gs.push_back(g);
+        }
+        // level 2 (outputs in place: 53, 55, 56)
+        l2_groups_ = (int)gs.size();
+        {
+            GroupDesc g = group(2, SLOT_L2 + 0, SLOT_L2 + 1);
+            add_out(g, SLOT_L2 + 0, 2, 0, DX, 1, DY);
+            gs.push_back(g);
+        }
+        {
+            GroupDesc g = group(2, SLOT_L2 + 1, SLOT_L2 + 2);
+            add_out(g, SLOT_L2 + 2, 2, 0, DX, 1, DY);
+            gs.push_back(g);
+        }
+        {
+            GroupDesc g = group(2, SLOT_L2 + 3, SLOT_L2 + 4);
+            add_out(g, SLOT_L2 + 3, 2, 0, DX, 1, DY);
+            gs.push_back(g);
+        }
+        // gradient op: field i in slot i -> slots 20 + 2i, 21 + 2i
+        grad_groups_ = (int)gs.size();
+        for (int i = 0; i < 16; ++i) {
+            GroupDesc g = group(1, i, 0);
+            add_out(g, 20 + 2 * i, 1, 0, DX);
+            add_out(g, 21 + 2 * i, 1, 0, DY);
+            gs.push_back(g);
+        }
+        // invariants: rho in slot 0 -> slots 1, 2
+        inv_groups_ = (int)gs.size();
+        {
+            GroupDesc g = group(1, 0, 0);
+            add_out(g, 1, 1, 0, DX);
+            add_out(g, 2, 1, 0, DY);
+            gs.push_back(g);
+        }
+        Status st = dalloc(&groups_, gs.size());
+        if (!st.good()) return st;
+        FFTLB_CU(cudaMemcpy(groups_, gs.data(), gs.size() * sizeof(GroupDesc), cudaMemcpyHostToDevice));
+        return Status::ok();
+    }
+
+    Status configure() {
+        const size_t cs = sizeof(C), rs = sizeof(real);
+        int dev = 0;
+        FFTLB_CU(cudaGetDevice(&dev));
+        int maxsm = 0;
+        FFTLB_CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const size_t budget = (size_t)maxsm - 2048;   // static shared memory headroom
+        // column tile width: largest of 8, 4, 2, 1 dividing h with the
+        // batched column FFT fitting the registers (TW ny <= 16 NT) and
+        // 3 tiles in shared memory
+        TW_ = 1;
+        for (int tw = 8; tw >= 1; tw >>= 1) {
+            if (h_ % tw) continue;
+            if ((size_t)tw * ny_ > 16 * NT) continue;
+            if ((size_t)(ny_ + 3 * tw * ny_) * cs > budget) continue;
+            TW_ = tw;
+            break;
+        }
+        smem_col1_ = (size_t)(ny_ + 2 * TW_ * ny_) * cs;
+        smem_col2_ = (size_t)(ny_ + 3 * TW_ * ny_) * cs;
+        B1_ = std::max(1, std::min(32, (16 * NT) / h_));
+        smem_k1_ = (size_t)(2 * h_ + B1_ * h_) * cs + 4 * nx_ * rs;
+        while (smem_k1_ > budget && B1_ > 1) {
+            --B1_;
+            smem_k1_ = (size_t)(2 * h_ + B1_ * h_) * cs + 4 * nx_ * rs;
+        }
+        smem_k3_ = (size_t)(2 * h_ + ND1 * h_) * cs;
+        B5_ = std::max(1, std::min(32, (16 * NT) / h_));
+        smem_k5_ = (size_t)(2 * h_ + 3 * h_ + B5_ * h_) * cs + NST * nx_ * rs;
+        while (smem_k5_ > budget && B5_ > 1) {
+            --B5_;
+            smem_k5_ = (size_t)(2 * h_ + 3 * h_ + B5_ * h_) * cs + NST * nx_ * rs;
+        }
+        smem_rows1_ = (size_t)3 * h_ * cs;
+        smem_inv_ = (size_t)4 * h_ * cs;
+        if (smem_k1_ > budget || smem_k3_ > budget || smem_k5_ > budget || smem_col2_ > budget)
+            return Status::err(FFTLB_ERR_ARG, "grid too large for shared-memory tiles");
+        FFTLB_CU(cudaFuncSetAttribute(k_row_forward_moments<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+        FFTLB_CU(cudaFuncSetAttribute(k_col<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+        FFTLB_CU(cudaFuncSetAttribute(k_row_level1<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+        FFTLB_CU(cudaFuncSetAttribute(k_row_final<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+        kp_.nx = nx_;
+        kp_.ny = ny_;
+        kp_.h = h_;
+        kp_.dx = (real)p_.dx;
+        kp_.dt = (real)p_.dt;
+        kp_.tau = (real)p_.tau;
+        kp_.a = (real)p_.a;
+        kp_.b = (real)p_.b;
+        kp_.K = (real)p_.K;
+        kp_.H = (real)p_.H;
+        kp_.q = (real)p_.q;
+        kp_.zeta = (real)p_.zeta;
+        kp_.scale = (real)(1.0 / ((double)nx_ * (double)ny_));
+        return Status::ok();
+    }
+
+    Status run_groups(int first, int count, int nin_max) {
+        const size_t sm = nin_max == 1 ? smem_col1_ : smem_col2_;
+        k_col<real><<<dim3(h_ / TW_, count), NT, sm, stream_>>>(spec_, groups_ + first, kxt_, kyt_, Wc_, kp_, TW_,
+                                                                nin_max + 0);
+        FFTLB_LAUNCHED("k_col");
+        return Status::ok();
+    }
+
+    Status stage(const real *cur, const real *base, real *out, real alpha, real beta) {
+        Status st;
+        if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
+        k_row_forward_moments<real><<<ny_, NT, smem_k1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, B1_);
+        FFTLB_LAUNCHED("k_row_forward_moments");
+        if (!(st = prof_end()).good()) return st;
+        if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
+        if (!(st = run_groups(conv_groups_, NMOV, 1)).good()) return st;
+        if (!(st = prof_end()).good()) return st;
+        if (!(st = prof_begin(KK_COL_LEVEL1)).good()) return st;
+        if (!(st = run_groups(l1_groups_, 5, 2)).good()) return st;
+        if (!(st = prof_end()).good()) return st;
+        if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
+        k_row_level1<real><<<ny_, NT, smem_k3_, stream_>>>(spec_, fields_, aux_, Wr_, Wp_, kp_);
+        FFTLB_LAUNCHED("k_row_level1");
+        if (!(st = prof_end()).good()) return st;
+        if (!(st = prof_begin(KK_COL_LEVEL2)).good()) return st;
+        if (!(st = run_groups(l2_groups_, 3, 2)).good()) return st;
+        if (!(st = prof_end()).good()) return st;
+        if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
+        k_row_final<real><<<ny_, NT, smem_k5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+                                                          Wp_, kp_, B5_);
+        FFTLB_LAUNCHED("k_row_final");
+        return prof_end();
+    }
+
+    Status sums(bool with_grad, double out[6]) {
+        k_moments<real><<<grid1d(), 256, 0, stream_>>>(f0_, fields_, N_);
+        FFTLB_LAUNCHED("k_moments");
+        if (with_grad) {
+            k_rows_forward<real, real><<<dim3(ny_, 1), NT, smem_rows1_, stream_>>>(fields_, spec_, 0, Wr_, Wp_, kp_);
+            FFTLB_LAUNCHED("k_rows_forward");
+            Status st = run_groups(inv_groups_, 1, 1);
+            if (!st.good()) return st;
+        }
+        k_invariant_rows<real><<<ny_, NT, smem_inv_, stream_>>>(spec_, fields_, partial_, Wr_, Wp_, kp_,
+                                                                with_grad ? 1 : 0);
+        FFTLB_LAUNCHED("k_invariant_rows");
+        k_reduce_partials<<<1, NT, 0, stream_>>>(partial_, ny_, red_);
+        FFTLB_LAUNCHED("k_reduce_partials");
+        FFTLB_CU(cudaMemcpyAsync(out, red_, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        FFTLB_CU(cudaStreamSynchronize(stream_));
+        return Status::ok();
+    }
+};
+
+}  // namespace fftlb

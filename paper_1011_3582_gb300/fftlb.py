@@ -1,0 +1,196 @@
+"""ctypes binding of libfftlb.so (C ABI in include/fftlb.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device buffers are passed as integer addresses (for example
+``tensor.data_ptr()`` of a CUDA tensor) with ``on_device=True``; host
+buffers as float64 C-contiguous numpy arrays.  Importing this module loads
+the library and raises if it has not been built (``build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfftlb.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libfftlb.so is not built: run paper_1011_3582_gb300.build.build() "
+                      "(or __graft_entry__.build()) first")
+_lib = ct.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = range(7)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_CUDA", "ERR_UNSTABLE", "ERR_TIMEOUT", "ERR_STATE"]
+
+EXPORTED = ["fftlb_create", "fftlb_set_fields", "fftlb_step", "fftlb_fields", "fftlb_get_f",
+            "fftlb_set_f", "fftlb_invariants", "fftlb_gradient", "fftlb_save", "fftlb_load",
+            "fftlb_destroy", "fftlb_last_error", "fftlb_launches_per_step", "fftlb_profile",
+            "fftlb_profile_read", "fftlb_kernel_name"]
+
+
+class fftlb_params(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int),
+                ("dx", ct.c_double), ("dt", ct.c_double), ("tau", ct.c_double),
+                ("a", ct.c_double), ("b", ct.c_double), ("K", ct.c_double), ("H", ct.c_double),
+                ("q", ct.c_double), ("zeta", ct.c_double),
+                ("window", ct.c_int), ("integrator", ct.c_int), ("precision", ct.c_int),
+                ("check_every", ct.c_int)]
+
+
+class fftlb_velset(ct.Structure):
+    _fields_ = [("nspeeds", ct.c_int), ("speeds", ct.POINTER(ct.c_double)), ("ndirs", ct.c_int)]
+
+
+_h = ct.c_void_p
+_p = ct.c_void_p
+_lib.fftlb_create.argtypes = [ct.POINTER(_h), ct.POINTER(fftlb_params), ct.POINTER(fftlb_velset), _p]
+_lib.fftlb_set_fields.argtypes = [_h, _p, _p, _p, _p, ct.c_int]
+_lib.fftlb_step.argtypes = [_h, ct.c_long, ct.POINTER(ct.c_long)]
+_lib.fftlb_fields.argtypes = [_h, _p, _p, _p, _p, ct.c_int]
+_lib.fftlb_get_f.argtypes = [_h, _p, ct.c_int]
+_lib.fftlb_set_f.argtypes = [_h, _p, ct.c_int]
+_lib.fftlb_invariants.argtypes = [_h, ct.POINTER(ct.c_double)]
+_lib.fftlb_gradient.argtypes = [_h, _p, _p, ct.c_int]
+_lib.fftlb_save.argtypes = [_h, ct.c_char_p]
+_lib.fftlb_load.argtypes = [_h, ct.c_char_p]
+_lib.fftlb_destroy.argtypes = [_h]
+_lib.fftlb_last_error.argtypes = [_h]
+_lib.fftlb_last_error.restype = ct.c_char_p
+_lib.fftlb_launches_per_step.argtypes = [_h]
+_lib.fftlb_launches_per_step.restype = ct.c_int
+_lib.fftlb_profile.argtypes = [_h, ct.c_int]
+_lib.fftlb_profile_read.argtypes = [_h, ct.POINTER(ct.c_double), ct.POINTER(ct.c_long),
+                                    ct.POINTER(ct.c_double), ct.c_int]
+_lib.fftlb_kernel_name.argtypes = [ct.c_int]
+_lib.fftlb_kernel_name.restype = ct.c_char_p
+for _n in EXPORTED:
+    if _n not in ("fftlb_last_error", "fftlb_launches_per_step", "fftlb_kernel_name"):
+        getattr(_lib, _n).restype = ct.c_int
+
+
+class FFTLBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+def _addr(x, on_device):
+    if x is None:
+        return None
+    if on_device:
+        return int(x) if isinstance(x, int) else int(x.data_ptr())
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+        raise TypeError("host buffers must be C-contiguous float64 numpy arrays")
+    return x.ctypes.data
+
+
+def params(nx, ny, dx=1.0 / 256, dt=1e-5, tau=1e-2, a=9.0 / 8.0, b=1.0 / 3.0, K=1e-5, H=0.0,
+           q=-0.004, zeta=0.0, window=4, integrator=3, precision=64, check_every=0):
+    """fftlb_params with the paper's defaults (Sec. 3)."""
+    return fftlb_params(nx, ny, dx, dt, tau, a, b, K, H, q, zeta, window, integrator, precision,
+                        check_every)
+
+
+class Handle:
+    """Owning wrapper of an fftlb_t.  Method names follow the C calls."""
+
+    def __init__(self, p: fftlb_params, speeds=None, stream=0):
+        self._h = _h()
+        vs = None
+        if speeds is not None:
+            arr = (ct.c_double * 4)(*speeds)
+            self._speeds = arr
+            vs = ct.byref(fftlb_velset(4, ct.cast(arr, ct.POINTER(ct.c_double)), 8))
+        self.params = p
+        st = _lib.fftlb_create(ct.byref(self._h), ct.byref(p), vs, ct.c_void_p(int(stream)))
+        if st != OK:
+            raise FFTLBError(st, _lib.fftlb_last_error(None).decode())
+
+    def _check(self, st):
+        if st != OK:
+            raise FFTLBError(st, _lib.fftlb_last_error(self._h).decode())
+
+    @property
+    def shape(self):
+        return (self.params.ny, self.params.nx)
+
+    def set_fields(self, rho, ux, uy, T, on_device=False):
+        a = [_addr(v, on_device) for v in (rho, ux, uy, T)]
+        self._check(_lib.fftlb_set_fields(self._h, *a, int(on_device)))
+
+    def step(self, nsteps=1):
+        done = ct.c_long(0)
+        st = _lib.fftlb_step(self._h, int(nsteps), ct.byref(done))
+        if st != OK:
+            err = FFTLBError(st, _lib.fftlb_last_error(self._h).decode())
+            err.steps_done = done.value
+            raise err
+        return done.value
+
+    def fields(self, rho=None, ux=None, uy=None, T=None, on_device=False):
+        if not on_device and rho is None and ux is None and uy is None and T is None:
+            rho, ux, uy, T = (np.empty(self.shape) for _ in range(4))
+        a = [_addr(v, on_device) for v in (rho, ux, uy, T)]
+        self._check(_lib.fftlb_fields(self._h, *a, int(on_device)))
+        return rho, ux, uy, T
+
+    def get_f(self, out=None, on_device=False):
+        if out is None:
+            out = np.empty((33,) + self.shape)
+        self._check(_lib.fftlb_get_f(self._h, _addr(out, on_device), int(on_device)))
+        return out
+
+    def set_f(self, f, on_device=False):
+        self._check(_lib.fftlb_set_f(self._h, _addr(f, on_device), int(on_device)))
+
+    def invariants(self):
+        out = (ct.c_double * 6)()
+        self._check(_lib.fftlb_invariants(self._h, out))
+        return dict(mass=out[0], px=out[1], py=out[2], eT=out[3], umax=out[4], time=out[5])
+
+    def gradient(self, g, out, nfields):
+        """g, out: device addresses (fp64 [nfields][ny][nx] and [2 nfields][ny][nx])."""
+        self._check(_lib.fftlb_gradient(self._h, _addr(g, True), _addr(out, True), int(nfields)))
+
+    def save(self, path):
+        self._check(_lib.fftlb_save(self._h, path.encode()))
+
+    def load(self, path):
+        self._check(_lib.fftlb_load(self._h, path.encode()))
+
+    def launches_per_step(self):
+        return _lib.fftlb_launches_per_step(self._h)
+
+    def profile(self, enable=True):
+        self._check(_lib.fftlb_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches, algorithmic bytes per launch)}."""
+        ms = (ct.c_double * 6)()
+        n = (ct.c_long * 6)()
+        by = (ct.c_double * 6)()
+        self._check(_lib.fftlb_profile_read(self._h, ms, n, by, 6))
+        return {_lib.fftlb_kernel_name(k).decode(): (ms[k], n[k], by[k]) for k in range(6)}
+
+    def close(self):
+        if self._h:
+            _lib.fftlb_destroy(self._h)
+            self._h = _h()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def lib():
+    return _lib

@@ -1,0 +1,64 @@
+"""Shared set-up of the GPU parity tests: configurations shaped like the
+paper's workloads and cached oracle runs."""
+import functools
+
+import numpy as np
+
+from oracle import fftlb_oracle as O
+from oracle import thermo as TH
+from paper_1011_3582_gb300 import workloads as W
+
+A49, B21 = 9.0 / 49.0, 2.0 / 21.0          # vdW constants of the benchmark configurations
+TC49 = 8 * A49 / (27 * B21)                # = 4/7
+RHOC49 = 1.0 / (3 * B21)                   # = 3.5
+
+
+def lib():
+    from paper_1011_3582_gb300 import build
+    build.build()
+    from paper_1011_3582_gb300 import fftlb
+    return fftlb
+
+
+def slab64():
+    """64x64 planar slab at T = 0.9 T_c, Maxwell densities in the central 32
+    rows with tanh edges of width 2, seed-42 noise U(-1e-4, 1e-4) on rho."""
+    T = 0.9 * TC49
+    rv, rl = TH.maxwell(T, A49, B21)
+    fields = W.slab(64, 64, rv, rl, T, y1=16, y2=48, width=2.0, noise=1e-4, seed=42)
+    return fields, dict(nx=64, ny=64, a=A49, b=B21)
+
+
+def droplet_ragged():
+    """48 x 96 (radix-3 axes) droplet of the paper's EOS at T = 0.95."""
+    rv, rl = TH.maxwell(0.95, 9 / 8, 1 / 3)
+    fields = W.droplet(96, 48, 14.0, rl, rv, 0.95, width=2.0)
+    return fields, dict(nx=96, ny=48, a=9 / 8, b=1 / 3)
+
+
+def oracle_params(kw, **extra):
+    d = dict(kw)
+    d.update(extra)
+    return O.Params(**{k: v for k, v in d.items() if k in O.Params.__dataclass_fields__})
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(name, nsteps, integrator, window=4):
+    fields, kw = {"slab64": slab64, "droplet_ragged": droplet_ragged}[name]()
+    p = oracle_params(kw, integrator=integrator, window=window)
+    f = O.init_equilibrium(*fields, p)
+    f = O.run(f, p, nsteps)
+    return f, O.moments(f), O.invariants(f, p)
+
+
+def gpu_run(fl, name, nsteps, integrator, precision, window=4):
+    fields, kw = {"slab64": slab64, "droplet_ragged": droplet_ragged}[name]()
+    p = fl.params(integrator=integrator, precision=precision, window=window, **kw)
+    with fl.Handle(p) as h:
+        h.set_fields(*fields)
+        h.step(nsteps)
+        return h.get_f(), h.fields(), h.invariants()
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)

@@ -1,0 +1,129 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+paper-shaped workloads.  Bar: FP64 path within 1e-9 relative per field after
+100 steps; FP32 path within the tolerances derived in the design doc (rounding of
+fp32 state and transforms, ~1e-6 relative per step, accumulated)."""
+import numpy as np
+import pytest
+
+from gpu_common import (A49, B21, TC49, RHOC49, droplet_ragged, gpu_run, lib, oracle_params, oracle_run,
+                        rel_err, slab64)
+from oracle import fftlb_oracle as O
+from paper_1011_3582_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fl():
+    return lib()
+
+
+def test_set_fields_builds_equilibrium(fl):
+    fields, kw = slab64()
+    p = fl.params(precision=64, **kw)
+    with fl.Handle(p) as h:
+        h.set_fields(*fields)
+        f = h.get_f()
+        r, ux, uy, T = h.fields()
+    fo = O.feq(*fields)
+    assert rel_err(f, fo) < 1e-14
+    assert rel_err(r, fields[0]) < 1e-14 and rel_err(T, fields[3]) < 1e-14
+    assert np.abs(ux).max() < 1e-14 and np.abs(uy).max() < 1e-14
+
+
+@pytest.mark.parametrize("integrator", [1, 3])
+def test_slab64_fp64_100_steps(fl, integrator):
+    f_o, (r_o, ux_o, uy_o, T_o), inv_o = oracle_run("slab64", 100, integrator)
+    f_g, (r_g, ux_g, uy_g, T_g), inv_g = gpu_run(fl, "slab64", 100, integrator, 64)
+    assert rel_err(r_g, r_o) < 1e-9
+    assert rel_err(ux_g, ux_o) < 1e-9
+    assert rel_err(uy_g, uy_o) < 1e-9
+    assert rel_err(T_g, T_o) < 1e-9
+    assert rel_err(f_g, f_o) < 1e-9
+    assert inv_g["mass"] == pytest.approx(inv_o["mass"], rel=1e-12)
+    assert inv_g["eT"] == pytest.approx(inv_o["eT"], rel=1e-9)
+    assert inv_g["umax"] == pytest.approx(inv_o["umax"], rel=1e-9)
+
+
+def test_slab64_fp32_100_steps(fl):
+    f_o, (r_o, ux_o, uy_o, T_o), inv_o = oracle_run("slab64", 100, 3)
+    f_g, (r_g, ux_g, uy_g, T_g), inv_g = gpu_run(fl, "slab64", 100, 3, 32)
+    assert rel_err(r_g, r_o) < 2e-6
+    assert rel_err(T_g, T_o) < 2e-6
+    assert rel_err(ux_g, ux_o) < 1e-3
+    assert rel_err(uy_g, uy_o) < 1e-3
+    assert inv_g["mass"] == pytest.approx(inv_o["mass"], rel=1e-6)
+
+
+@pytest.mark.parametrize("window", [0, 1, 2, 3])
+def test_windows_fp64(fl, window):
+    f_o, mo, _ = oracle_run("slab64", 10, 1, window)
+    f_g, mg, _ = gpu_run(fl, "slab64", 10, 1, 64, window)
+    for a, b in zip(mg, mo):
+        assert rel_err(a, b) < 1e-10
+
+
+def test_ragged_radix3_grid_fp64(fl):
+    f_o, mo, inv_o = oracle_run("droplet_ragged", 20, 3)
+    f_g, mg, inv_g = gpu_run(fl, "droplet_ragged", 20, 3, 64)
+    for a, b in zip(mg, mo):
+        assert rel_err(a, b) < 1e-10
+    assert rel_err(f_g, f_o) < 1e-10
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (8, 4), (4, 12), (6, 8)])
+def test_tiny_grids(fl, shape):
+    ny, nx = shape
+    fields = W.smooth_random(nx, ny, seed=11, rho0=1.2, T0=0.9, amp=0.05, umax=0.02)
+    kw = dict(nx=nx, ny=ny, dx=1 / 64, K=1e-4)
+    p = oracle_params(kw, integrator=3)
+    f_o = O.run(O.init_equilibrium(*fields, p), p, 5)
+    with fl.Handle(fl.params(precision=64, integrator=3, **kw)) as h:
+        h.set_fields(*fields)
+        h.step(5)
+        f_g = h.get_f()
+    assert rel_err(f_g, f_o) < 1e-12
+
+
+def test_conservation_and_invariants_fp64(fl):
+    fields, kw = slab64()
+    with fl.Handle(fl.params(precision=64, integrator=3, **kw)) as h:
+        h.set_fields(*fields)
+        i0 = h.invariants()
+        h.step(50)
+        i1 = h.invariants()
+    assert abs(i1["mass"] - i0["mass"]) < 1e-13 * i0["mass"]
+    assert abs(i1["px"]) < 1e-14 * i0["mass"] and abs(i1["py"]) < 1e-14 * i0["mass"]
+    assert i1["time"] == pytest.approx(50 * 1e-5)
+
+
+def test_checkpoint_resume_is_bit_identical(fl, tmp_path):
+    fields, kw = slab64()
+    p = fl.params(precision=64, integrator=3, **kw)
+    path = str(tmp_path / "ckpt.bin")
+    with fl.Handle(p) as h:
+        h.set_fields(*fields)
+        h.step(5)
+        h.save(path)
+        h.step(5)
+        f_a = h.get_f()
+    with fl.Handle(p) as h2:
+        h2.load(path)
+        assert h2.invariants()["time"] == pytest.approx(5e-5)
+        h2.step(5)
+        f_b = h2.get_f()
+    assert np.array_equal(f_a, f_b)
+
+
+def test_unstable_state_is_reported_not_trapped(fl):
+    """Host-side failure detection: an unphysical initial temperature is
+    reported as ERR_UNSTABLE with the step count."""
+    fields, kw = slab64()
+    rho, ux, uy, T = (x.copy() for x in fields)
+    T[5, 7] = -0.3
+    with fl.Handle(fl.params(precision=64, integrator=1, check_every=1, **kw)) as h:
+        h.set_fields(rho, ux, uy, T)
+        with pytest.raises(fl.FFTLBError) as ei:
+            h.step(3)
+        assert ei.value.status == fl.ERR_UNSTABLE
+        assert ei.value.steps_done == 1

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+include/fftlb.h declares, and rejects invalid arguments before touching
+the device."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from paper_1011_3582_gb300 import build
+    build.build()
+    from paper_1011_3582_gb300 import fftlb
+    return fftlb
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fftlb_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(fl):
+    names = declared_functions()
+    assert "fftlb_create" in names and "fftlb_step" in names
+    lib = ct.CDLL(fl.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(fl.EXPORTED) <= names
+
+
+def test_params_struct_layout_matches_header(fl):
+    # int nx, ny; 9 doubles; 4 ints  (x86-64 / aarch64 LP64 layout)
+    assert ct.sizeof(fl.fftlb_params) == 8 + 9 * 8 + 4 * 4
+
+
+@pytest.mark.parametrize("kw", [dict(nx=10), dict(ny=6 * 5), dict(nx=2), dict(tau=0.0), dict(window=5),
+                                dict(integrator=2), dict(precision=16)])
+def test_create_rejects_bad_arguments_without_device_work(fl, kw):
+    base = dict(nx=16, ny=16)
+    base.update(kw)
+    p = fl.params(**base)
+    with pytest.raises(fl.FFTLBError) as ei:
+        fl.Handle(p)
+    assert ei.value.status == fl.ERR_ARG
+    assert len(str(ei.value)) > 10
+
+
+def test_null_handle_calls_return_arg_error(fl):
+    lib = fl.lib()
+    assert lib.fftlb_step(None, 1, None) == fl.ERR_ARG
+    assert lib.fftlb_invariants(None, None) == fl.ERR_ARG
+    assert lib.fftlb_destroy(None) == fl.OK
