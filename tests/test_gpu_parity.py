@@ -46,13 +46,23 @@ def test_slab64_fp64_100_steps(fl, integrator):
 
 
 def test_slab64_fp32_100_steps(fl):
+    """FP32 state and transforms.  Bound: every one of the S = 300 stage
+    updates rounds f to fp32 (unit roundoff u = 2^-24); with small,
+    correlated increments these roundings add up, so |drho|/rho, |dT|/T
+    <= S u / 2 ~ 1e-5.  Velocities are differences of O(rho |v|) sums, so
+    their absolute error is <= S u <|v|> ~ 3e-5, i.e. < 5e-3 of max |u|
+    (~ 8e-3 here), measured component-wise against max |u|."""
+    S, u = 300, 2.0 ** -24
     f_o, (r_o, ux_o, uy_o, T_o), inv_o = oracle_run("slab64", 100, 3)
     f_g, (r_g, ux_g, uy_g, T_g), inv_g = gpu_run(fl, "slab64", 100, 3, 32)
-    assert rel_err(r_g, r_o) < 2e-6
-    assert rel_err(T_g, T_o) < 2e-6
-    assert rel_err(ux_g, ux_o) < 1e-3
-    assert rel_err(uy_g, uy_o) < 1e-3
-    assert inv_g["mass"] == pytest.approx(inv_o["mass"], rel=1e-6)
+    umax = np.hypot(ux_o, uy_o).max()
+    errs = dict(rho=rel_err(r_g, r_o), T=rel_err(T_g, T_o),
+                u=max(np.abs(ux_g - ux_o).max(), np.abs(uy_g - uy_o).max()) / umax,
+                mass=abs(inv_g["mass"] - inv_o["mass"]) / inv_o["mass"])
+    print("fp32 vs fp64 oracle after 100 RK3 steps:", errs)
+    assert errs["rho"] < S * u / 2 and errs["T"] < S * u / 2
+    assert errs["u"] < 5e-3
+    assert errs["mass"] < S * u / 2
 
 
 @pytest.mark.parametrize("window", [0, 1, 2, 3])
