@@ -151,6 +151,29 @@ fftlb_status fftlb_profile(fftlb_t h, int enable);
 fftlb_status fftlb_profile_read(fftlb_t h, double *ms, long *launches, double *bytes, int nkinds);
 const char *fftlb_kernel_name(int kind);
 
+/* Windowed spectral gradient of one fp64 device field g[ny][nx] into
+ * out[2][ny][nx] (out[0] = D_x g, out[1] = D_y g), like fftlb_gradient with
+ * nfields = 1, but without a handle and without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not call cudaMalloc/cudaFree while they run (a plug-in inside a
+ * framework whose caching allocator owns the GPU's memory, or a loop that
+ * cannot afford an allocation's implicit device synchronisation).  Its
+ * intermediate spectra and tables live in one fixed array in device global
+ * memory (about 1.6 MB), defined by the library and held on every GPU that
+ * loads it until the process exits.
+ *  - Limits: nx, ny even 2^p 3^q in [4, 1024] and nx * ny <= 65536; larger
+ *    grids return FFTLB_ERR_ARG with a message (fftlb_last_error(NULL)).
+ *  - The first call on a device looks up the array's device address and
+ *    sets a kernel attribute (once per device, with that device current);
+ *    make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents:
+ *    calls that overlap on the GPU (several streams or host threads) race
+ *    and give wrong results.  Serialise them.
+ *  - Asynchronous on cuda_stream (a cudaStream_t, may be NULL); g and out
+ *    are caller-owned device buffers. */
+fftlb_status fftlb_gradient_static(const double *g, double *out, int nx, int ny,
+                                   double dx, int window, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

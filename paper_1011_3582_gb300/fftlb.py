@@ -27,7 +27,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_CUDA", "ERR_UNSTABLE", "ERR_TIM
 EXPORTED = ["fftlb_create", "fftlb_set_fields", "fftlb_step", "fftlb_fields", "fftlb_get_f",
             "fftlb_set_f", "fftlb_invariants", "fftlb_gradient", "fftlb_save", "fftlb_load",
             "fftlb_destroy", "fftlb_last_error", "fftlb_launches_per_step", "fftlb_profile",
-            "fftlb_profile_read", "fftlb_kernel_name"]
+            "fftlb_profile_read", "fftlb_kernel_name", "fftlb_gradient_static"]
 
 
 class fftlb_params(ct.Structure):
@@ -63,6 +63,7 @@ _lib.fftlb_launches_per_step.restype = ct.c_int
 _lib.fftlb_profile.argtypes = [_h, ct.c_int]
 _lib.fftlb_profile_read.argtypes = [_h, ct.POINTER(ct.c_double), ct.POINTER(ct.c_long),
                                     ct.POINTER(ct.c_double), ct.c_int]
+_lib.fftlb_gradient_static.argtypes = [_p, _p, ct.c_int, ct.c_int, ct.c_double, ct.c_int, _p]
 _lib.fftlb_kernel_name.argtypes = [ct.c_int]
 _lib.fftlb_kernel_name.restype = ct.c_char_p
 for _n in EXPORTED:
@@ -190,6 +191,15 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+def gradient_static(g, out, nx, ny, dx=1.0 / 256, window=4, stream=0):
+    """fftlb_gradient_static: D_x, D_y of one fp64 device field without any
+    device allocation (g, out: device addresses of [ny][nx] and [2][ny][nx])."""
+    st = _lib.fftlb_gradient_static(_addr(g, True), _addr(out, True), int(nx), int(ny), float(dx),
+                                    int(window), ct.c_void_p(int(stream)))
+    if st != OK:
+        raise FFTLBError(st, _lib.fftlb_last_error(None).decode())
 
 
 def lib():
