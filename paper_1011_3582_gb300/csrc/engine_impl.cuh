@@ -26,9 +26,13 @@
 // row-Nyquist value packed into the imaginary part of column 0.
 #pragma once
 
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(NT) k_row_forward_moments(const real *__restri
                                                             const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                             KP<real> P, int B) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
     C *Wr = reinterpret_cast<C *>(smem_raw);
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_col(typename cplx_of<real>::type *__rest
                                             const typename cplx_of<real>::type *__restrict__ Wc_g, KP<real> P,
                                             int TW, int nin_max) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ GroupDesc g;
     const int ny = P.ny, h = P.h, tid = threadIdx.x;
     const size_t slot = (size_t)ny * h;
@@ -330,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_row_level1(typename cplx_of<real>::type 
                                                    const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                    KP<real> P) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
     C *Wr = reinterpret_cast<C *>(smem_raw);
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(NT) k_row_final(const typename cplx_of<real>::
                                                   const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P,
                                                   int B) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
     C *Wr = reinterpret_cast<C *>(smem_raw);
@@ -555,7 +559,7 @@ __global__ void __launch_bounds__(NT) k_rows_forward(const TIn *__restrict__ in,
                                                      int slot0, const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                      const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, fi = blockIdx.y, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
     C *Wr = reinterpret_cast<C *>(smem_raw);
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(NT) k_rows_inverse(const typename cplx_of<real
                                                      const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                      const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, fi = blockIdx.y, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
     C *Wr = reinterpret_cast<C *>(smem_raw);
@@ -603,7 +607,7 @@ __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<re
                                                        const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                        KP<real> P, int with_grad) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ double red[6][NT];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
@@ -679,6 +683,12 @@ static __global__ void k_reduce_partials(const double *partial, int ny, double *
     }
     if (tid < 6) out[tid] = red[tid][0];
 }
+
+}  // namespace fftlb
+
+#include "kernels_pipe.cuh"
+
+namespace fftlb {
 
 // ---------------------------------------------------------------------------
 // host side
@@ -787,6 +797,10 @@ class EngineT : public Engine {
     }
 
     Status fields(double *rho, double *ux, double *uy, double *T, bool on_device) override {
+        {
+            Status st = check_err();
+            if (!st.good()) return st;
+        }
         k_moments<real><<<grid1d(), 256, 0, stream_>>>(f0_, fields_, N_);
         FFTLB_LAUNCHED("k_moments");
         double *tmp = reinterpret_cast<double *>(scratch_d_);
@@ -881,6 +895,13 @@ class EngineT : public Engine {
     int TW_ = 1;
     size_t smem_k1_ = 0, smem_k3_ = 0, smem_k5_ = 0, smem_col1_ = 0, smem_col2_ = 0, smem_rows1_ = 0, smem_inv_ = 0;
     int B1_ = 1, B5_ = 1;
+    // pipelined kernels
+    int *err_ = nullptr;
+    int nsm_ = 1;
+    int CH1_ = 8, SMAX1_ = 1, grid1_ = 1, NHB5_ = 1, WR3_ = 1, CH5_ = 8, grid5_ = 1, SMAX5_ = 1, BOXR_ = 1;
+    int TWc_ = 1, TWl_ = 1, gridc_ = 1, gridl_ = 1;
+    size_t smem1_ = 0, smem3_ = 0, smem5_ = 0, smemc_ = 0, smeml_ = 0;
+    CUtensorMap tmap_conv_{}, tmap_l1_{};
     // profiling
     bool prof_ = false;
     struct ProfEv {
@@ -1055,6 +1076,8 @@ class EngineT : public Engine {
         if (!(st = dalloc(&Wc_, (size_t)ny_)).good()) return st;
         if (!(st = dalloc(&partial_, (size_t)ny_ * 6)).good()) return st;
         if (!(st = dalloc(&red_, 8)).good()) return st;
+        if (!(st = dalloc(&err_, 4)).good()) return st;
+        FFTLB_CU(cudaMemset(err_, 0, 4 * sizeof(int)));
         // fp64 staging for conversions: 33 N doubles (reuses nothing else)
         double *sc = nullptr;
         if (!(st = dalloc(&sc, Q * N_)).good()) return st;
@@ -1263,6 +1286,138 @@ class EngineT : public Engine {
         kp_.q = (real)p_.q;
         kp_.zeta = (real)p_.zeta;
         kp_.scale = (real)(1.0 / ((double)nx_ * (double)ny_));
+        return configure_pipe(budget);
+    }
+
+    static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+        static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+        if (!fn) {
+            void *p = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        }
+        return fn;
+    }
+
+    // the spectrum arena as a 2-D tensor {2h reals, NSLOT ny rows}, boxes
+    // of {2 TW reals, BOXR rows}
+    Status make_tmap(CUtensorMap *m, int TW) {
+        auto enc = tensor_map_encoder();
+        if (!enc) return Status::err(FFTLB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        cuuint64_t dims[2] = {(cuuint64_t)(2 * h_), (cuuint64_t)NSLOT * ny_};
+        cuuint64_t strides[1] = {(cuuint64_t)(2 * h_) * sizeof(real)};
+        cuuint32_t box[2] = {(cuuint32_t)(2 * TW), (cuuint32_t)BOXR_};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = enc(m, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                         (void *)spec_, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return Status::err(FFTLB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+        return Status::ok();
+    }
+
+    template <typename K> Status occupancy(K kernel, int nthreads, size_t smem, int *blocks) {
+        FFTLB_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FFTLB_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, nthreads, smem));
+        return Status::ok();
+    }
+
+    Status configure_pipe(size_t budget) {
+        const size_t cs = sizeof(C), rs = sizeof(real);
+        constexpr int NT = KCfg<real>::NT;
+        if (((size_t)nx_ * rs) % 16 != 0)
+            return Status::err(FFTLB_ERR_ARG, "rows must be a multiple of 16 bytes (fp32 needs nx divisible by 4)");
+        int dev = 0;
+        FFTLB_CU(cudaGetDevice(&dev));
+        FFTLB_CU(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+        Status st;
+        int nb = 0;
+        const size_t ph = (size_t)padded_len(h_);
+        SMAX1_ = (nx_ + NT - 1) / NT;
+        SMAX1_ = SMAX1_ <= 1 ? 1 : (SMAX1_ <= 2 ? 2 : 4);
+        SMAX5_ = SMAX1_;
+        // K1: chunks of 6..8 rows (>= 6 for the level-1 rows)
+        CH1_ = 0;
+        for (int ch = 8; ch >= 6; --ch) {
+            const size_t sm = smem_bytes({h_ * cs, h_ * cs, (size_t)ch * nx_ * rs, (size_t)ch * nx_ * rs, ch * ph * cs});
+            if (sm <= budget) {
+                CH1_ = ch;
+                smem1_ = sm;
+                break;
+            }
+        }
+        if (!CH1_) return Status::err(FFTLB_ERR_ARG, "grid too large for the row kernel");
+        if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, smem1_, &nb);
+        else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, smem1_, &nb);
+        else st = occupancy(k1_pipe<real, 4>, NT, smem1_, &nb);
+        if (!st.good()) return st;
+        grid1_ = std::min(ny_, std::max(1, nb) * nsm_);
+        // column kernels: box height divides ny; widest tile that fits
+        BOXR_ = 1;
+        for (int d = std::min(ny_, 256); d >= 1; --d)
+            if (ny_ % d == 0) {
+                BOXR_ = d;
+                break;
+            }
+        const size_t pny = (size_t)padded_len(ny_);
+        auto pick_tw = [&](bool multi, int *tw_out, size_t *sm_out) -> bool {
+            for (int tw = 8; tw >= 1; tw >>= 1) {
+                if (h_ % tw) continue;
+                if ((2 * tw * rs) % 16) continue;   // tensor box row: whole 16-byte units
+                const size_t tile = (size_t)tw * ny_ * cs, ptile = (size_t)tw * pny * cs;
+                const size_t sm = multi ? smem_bytes({ny_ * cs, 2 * tile, 2 * tile, ptile, ptile})
+                                        : smem_bytes({ny_ * cs, tile, tile, ptile});
+                if (sm > budget) continue;
+                *tw_out = tw;
+                *sm_out = sm;
+                return true;
+            }
+            return false;
+        };
+        if (!pick_tw(false, &TWc_, &smemc_) || !pick_tw(true, &TWl_, &smeml_))
+            return Status::err(FFTLB_ERR_ARG, "grid too large for the column kernel");
+        if (!(st = occupancy(kcol_pipe<real, false>, NT, smemc_, &nb)).good()) return st;
+        gridc_ = std::max(1, nb) * nsm_;
+        if (!(st = occupancy(kcol_pipe<real, true>, NT, smeml_, &nb)).good()) return st;
+        gridl_ = std::max(1, nb) * nsm_;
+        if (!(st = make_tmap(&tmap_conv_, TWc_)).good()) return st;
+        if (!(st = make_tmap(&tmap_l1_, TWl_)).good()) return st;
+        // K3
+        WR3_ = 0;
+        for (int wr = ND1; wr >= 1; --wr) {
+            smem3_ = smem_bytes({h_ * cs, h_ * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs, (size_t)2 * nx_ * rs});
+            if (smem3_ <= budget) {
+                WR3_ = wr;
+                break;
+            }
+        }
+        if (!WR3_) return Status::err(FFTLB_ERR_ARG, "grid too large for the level-1 row kernel");
+        if (!(st = occupancy(k3_pipe<real>, NT3, smem3_, &nb)).good()) return st;
+        // K5: two head buffers when they fit, chunks of up to 8 rows
+        CH5_ = 0;
+        for (int nhb = 2; nhb >= 1 && !CH5_; --nhb) {
+            for (int ch = CHMAX5; ch >= 2; ch -= 2) {
+                const size_t head = (size_t)NHEAD * nx_ * rs;
+                const size_t sm =
+                    smem_bytes({h_ * cs, h_ * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
+                                (size_t)ch * nx_ * rs, (size_t)std::max(ch, 3) * ph * cs});
+                if (sm <= budget && (ch >= 4 || nhb == 1)) {
+                    CH5_ = ch;
+                    NHB5_ = nhb;
+                    smem5_ = sm;
+                    break;
+                }
+            }
+        }
+        if (!CH5_) return Status::err(FFTLB_ERR_ARG, "grid too large for the final row kernel");
+        if (SMAX5_ == 1) st = occupancy(k5_pipe<real, 1>, NT, smem5_, &nb);
+        else if (SMAX5_ == 2) st = occupancy(k5_pipe<real, 2>, NT, smem5_, &nb);
+        else st = occupancy(k5_pipe<real, 4>, NT, smem5_, &nb);
+        if (!st.good()) return st;
+        grid5_ = std::min(ny_, std::max(1, nb) * nsm_);
         return Status::ok();
     }
 
@@ -1274,33 +1429,70 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
+    Status launch_col(int first, int count, bool level1) {
+        if (level1)
+            kcol_pipe<real, true><<<gridl_, KCfg<real>::NT, smeml_, stream_>>>(spec_, groups_ + first, count, kxt_,
+                                                                               kyt_, Wc_, kp_, TWl_, BOXR_, tmap_l1_,
+                                                                               err_);
+        else
+            kcol_pipe<real, false><<<gridc_, KCfg<real>::NT, smemc_, stream_>>>(
+                spec_, groups_ + first, count, kxt_, kyt_, Wc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
+        FFTLB_LAUNCHED("kcol_pipe");
+        return Status::ok();
+    }
+
     Status stage(const real *cur, const real *base, real *out, real alpha, real beta) {
         Status st;
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
-        k_row_forward_moments<real><<<ny_, NT, smem_k1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, B1_);
-        FFTLB_LAUNCHED("k_row_forward_moments");
+        if (SMAX1_ == 1)
+            k1_pipe<real, 1><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, CH1_, err_);
+        else if (SMAX1_ == 2)
+            k1_pipe<real, 2><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, CH1_, err_);
+        else
+            k1_pipe<real, 4><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, CH1_, err_);
+        FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
-        if (!(st = run_groups(conv_groups_, NMOV, 1)).good()) return st;
+        if (!(st = launch_col(conv_groups_, NMOV, false)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL1)).good()) return st;
-        if (!(st = run_groups(l1_groups_, 5, 2)).good()) return st;
+        if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
-        k_row_level1<real><<<ny_, NT, smem_k3_, stream_>>>(spec_, fields_, aux_, Wr_, Wp_, kp_);
-        FFTLB_LAUNCHED("k_row_level1");
+        k3_pipe<real><<<ny_, NT3, smem3_, stream_>>>(spec_, fields_, aux_, Wr_, Wp_, kp_, WR3_, err_);
+        FFTLB_LAUNCHED("k3_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL2)).good()) return st;
-        if (!(st = run_groups(l2_groups_, 3, 2)).good()) return st;
+        if (!(st = launch_col(l2_groups_, 3, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
-        k_row_final<real><<<ny_, NT, smem_k5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
-                                                          Wp_, kp_, B5_);
-        FFTLB_LAUNCHED("k_row_final");
+        if (SMAX5_ == 1)
+            k5_pipe<real, 1><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+                                                               Wp_, kp_, CH5_, NHB5_, err_);
+        else if (SMAX5_ == 2)
+            k5_pipe<real, 2><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+                                                               Wp_, kp_, CH5_, NHB5_, err_);
+        else
+            k5_pipe<real, 4><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+                                                               Wp_, kp_, CH5_, NHB5_, err_);
+        FFTLB_LAUNCHED("k5_pipe");
         return prof_end();
     }
 
+    // device error word (bounded waits that ran out)
+    Status check_err() {
+        int e = 0;
+        FFTLB_CU(cudaMemcpyAsync(&e, err_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+        FFTLB_CU(cudaStreamSynchronize(stream_));
+        if (e) return Status::err(FFTLB_ERR_TIMEOUT, "a bounded device wait ran out (error word " + std::to_string(e) + ")");
+        return Status::ok();
+    }
+
     Status sums(bool with_grad, double out[6]) {
+        {
+            Status st = check_err();
+            if (!st.good()) return st;
+        }
         k_moments<real><<<grid1d(), 256, 0, stream_>>>(f0_, fields_, N_);
         FFTLB_LAUNCHED("k_moments");
         if (with_grad) {

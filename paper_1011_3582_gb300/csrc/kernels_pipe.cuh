@@ -1,0 +1,768 @@
+// Pipelined kernels of one FFT-LB stage (arXiv:1011.3582; the stage is
+// described at the top of engine_impl.cuh).  Every kernel stages its global
+// inputs into shared memory with asynchronous bulk / tensor copies
+// (async_copy.cuh) so that the HBM traffic of the next job overlaps the
+// transforms of the current one, and transforms out of place between the
+// staged (unpadded) buffer and a padded work buffer (pp_fft):
+//   k1_pipe    persistent over rows; chunks of CH distribution rows,
+//              double-buffered; moments accumulate in registers.
+//   kcol_pipe  persistent over (group, column tile) jobs; TW-wide column
+//              tiles fetched by 2-D tensor copies, double-buffered.
+//   k3_pipe    one row per block: 15 derivative rows + rho, T.
+//   k5_pipe    persistent over rows; the per-row head (level-2 spectra,
+//              fields, aux) and CH-row chunks of convection spectra are
+//              prefetched.
+#pragma once
+
+#include "async_copy.cuh"
+
+#ifndef FFTLB_NT32
+#define FFTLB_NT32 512
+#endif
+#ifndef FFTLB_NT64
+#define FFTLB_NT64 256
+#endif
+
+namespace fftlb {
+
+// (offsets from the 1024-byte aligned dynamic base, so that the compiler
+// keeps every derived pointer in the shared address space)
+struct SmemCursor {
+    unsigned char *base;
+    unsigned off;
+    __device__ __forceinline__ void *take(size_t bytes) {
+        off = (off + 127u) & ~127u;
+        void *p = base + off;
+        off += (unsigned)bytes;
+        return p;
+    }
+};
+
+inline size_t smem_bytes(std::initializer_list<size_t> parts) {
+    size_t s = 0;
+    for (size_t b : parts) s = ((s + 127) & ~size_t(127)) + b;
+    return s;
+}
+
+// threads per block of the persistent kernels, per precision
+template <typename real> struct KCfg;
+template <> struct KCfg<float> {
+    static constexpr int NT = FFTLB_NT32;
+};
+template <> struct KCfg<double> {
+    static constexpr int NT = FFTLB_NT64;
+};
+
+template <typename C>
+__device__ __forceinline__ void load_tab(C *dst, const C *src, int n, int nthr) {
+    for (int i = threadIdx.x; i < n; i += nthr) dst[i] = src[i];
+}
+
+// real value x of row r of a packed-complex row buffer in layout L
+template <typename real>
+__device__ __forceinline__ real real_at(const typename cplx_of<real>::type *buf, Lay L, int r, int x) {
+    return reinterpret_cast<const real *>(buf)[2 * L(r, x >> 1) + (x & 1)];
+}
+
+// Transforms of nrows rows of A (layout la) through a work buffer of wrows
+// padded rows, a chunk at a time; results always end in A.
+template <int DIR, typename C>
+__device__ void rows_fft_to_A(C *A, Lay la, C *wk, Lay lb, int n, int nrows, int wrows, const C *W, int nthr) {
+    for (int r0 = 0; r0 < nrows; r0 += wrows) {
+        const int nb = min(wrows, nrows - r0);
+        C *a = A + (size_t)r0 * la.bs;
+        const int w = pp_fft<DIR, false>(a, la, wk, lb, n, nb, W, (int)threadIdx.x, nthr);
+        if (w) {
+            for (int i = threadIdx.x; i < nb * n; i += nthr) {
+                const int r = i / n, e = i - r * n;
+                a[la(r, e)] = wk[lb(r, e)];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1: moments + forward row transforms (persistent, double-buffered)
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__device__ __forceinline__ void k1_issue(const real *f, real *dst, uint64_t *bar, int j, int nchunk, int CH, int nx,
+                                         size_t N) {
+    const int ri = j / nchunk, c = j - ri * nchunk;
+    const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int i0 = c * CH, nf = min(CH, Q - i0);
+    const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
+    mbar_expect_tx(bar, (uint32_t)nf * rowbytes);
+    for (int r = 0; r < nf; ++r)
+        bulk_g2s(dst + (size_t)r * nx, f + (size_t)(i0 + r) * N + (size_t)y * nx, rowbytes, bar);
+}
+
+template <typename real, int SMAX>
+__global__ void __launch_bounds__(KCfg<real>::NT, 1) k1_pipe(const real *__restrict__ f,
+                                                             typename cplx_of<real>::type *spec,
+                                                             real *__restrict__ fields,
+                                                             const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                             const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                             KP<real> P, int CH, int *err) {
+    using C = typename cplx_of<real>::type;
+    constexpr int NT = KCfg<real>::NT;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1;
+    const int nx = P.nx, ny = P.ny, h = P.h, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    const int ph = padded_len(h);
+    SmemCursor sc{smem_raw, 0u};
+    C *Wr = (C *)sc.take(h * sizeof(C));
+    C *Wp = (C *)sc.take(h * sizeof(C));
+    real *buf0 = (real *)sc.take((size_t)CH * nx * sizeof(real));
+    real *buf1 = (real *)sc.take((size_t)CH * nx * sizeof(real));
+    C *wk = (C *)sc.take((size_t)CH * ph * sizeof(C));
+    const Lay la{h, 1, 0}, lb{ph, 1, 1};
+    const int nchunk = (Q + CH - 1) / CH;
+    const int nrows = (int)blockIdx.x < ny ? (ny - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs = nrows * nchunk;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(Wr, Wr_g, h, NT);
+    load_tab(Wp, Wp_g, h, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (njobs > 0) k1_issue(f, buf0, &bar0, 0, nchunk, CH, nx, N);
+        if (njobs > 1) k1_issue(f, buf1, &bar1, 1, nchunk, CH, nx, N);
+    }
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = njobs > 0, pend1 = njobs > 1;
+    real a0[SMAX], a1[SMAX], a2[SMAX], a3[SMAX];
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) a0[s] = a1[s] = a2[s] = a3[s] = real(0);
+    for (int j = 0; j < njobs; ++j) {
+        const bool odd = j & 1;
+        uint64_t *bar = odd ? &bar1 : &bar0;
+        const int ri = j / nchunk, c = j - ri * nchunk;
+        const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int i0 = c * CH, nf = min(CH, Q - i0);
+        if (!block_wait(bar, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        real *B = odd ? buf1 : buf0;
+        C *Bc = reinterpret_cast<C *>(B);
+        for (int r = 0; r < nf; ++r) {
+            const int i = i0 + r;
+            const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
+#pragma unroll
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x < nx) {
+                    const real v = B[(size_t)r * nx + x];
+                    a0[s] += v;
+                    a1[s] += vx * v;
+                    a2[s] += vy * v;
+                    a3[s] += v2 * v;
+                }
+            }
+        }
+        __syncthreads();
+        const int r0 = (i0 == 0) ? 1 : 0;   // the rest velocity is not transformed
+        if (nf > r0) {
+            const int w = pp_fft<-1, false>(Bc + (size_t)r0 * h, la, wk, lb, h, nf - r0, Wr, tid, NT);
+            C *res = w ? wk : Bc + (size_t)r0 * h;
+            const Lay lr = w ? lb : la;
+            r2c_post_l(res, lr, h, nf - r0, Wp, tid, NT);
+            __syncthreads();
+            for (int r = r0; r < nf; ++r) {
+                C *dst = spec + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
+                for (int k = tid; k < h; k += NT) dst[k] = res[lr(r - r0, k)];
+            }
+        }
+        if (c == nchunk - 1) {
+            __syncthreads();
+            // moments (Eqs. 7-9) and the level-1 fields rho, ux, uy, T, Pi, g
+#pragma unroll
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x < nx) {
+                    const real rho = a0[s], ux = a1[s] / rho, uy = a2[s] / rho;
+                    const real T = real(0.5) * (a3[s] / rho - (ux * ux + uy * uy));
+                    const size_t o = (size_t)y * nx + x;
+                    fields[o] = rho;
+                    fields[N + o] = ux;
+                    fields[2 * N + o] = uy;
+                    fields[3 * N + o] = T;
+                    B[x] = rho;
+                    B[nx + x] = ux;
+                    B[2 * nx + x] = uy;
+                    B[3 * nx + x] = T;
+                    B[4 * nx + x] = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;   // Eq. 18
+                    B[5 * nx + x] = (P.K + P.H * T) / T;                                          // M / T
+                }
+                a0[s] = a1[s] = a2[s] = a3[s] = real(0);
+            }
+            __syncthreads();
+            const int w = pp_fft<-1, false>(Bc, la, wk, lb, h, 6, Wr, tid, NT);
+            C *res = w ? wk : Bc;
+            const Lay lr = w ? lb : la;
+            r2c_post_l(res, lr, h, 6, Wp, tid, NT);
+            __syncthreads();
+            for (int r = 0; r < 6; ++r) {
+                C *dst = spec + (size_t)(SLOT_RHO + r) * slot + (size_t)y * h;
+                for (int k = tid; k < h; k += NT) dst[k] = res[lr(r, k)];
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && j + 2 < njobs) {
+            k1_issue(f, B, bar, j + 2, nchunk, CH, nx, N);
+            if (odd) pend1 = true;
+            else pend0 = true;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass (persistent over (group, tile) jobs, double-buffered)
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__device__ __forceinline__ typename cplx_of<real>::type mult_apply(real c0, real c1, real c2, real c3, real c4,
+                                                                    real ax, real ay,
+                                                                    typename cplx_of<real>::type v) {
+    using C = typename cplx_of<real>::type;
+    const real mr = c2 * ax * ax + c3 * ay * ay + c4 * ax * ay;
+    const real mi = c0 * ax + c1 * ay;
+    return C{mr * v.x - mi * v.y, mr * v.y + mi * v.x};
+}
+
+// out = scale * sum_t M_t(kx, ky) X_t over a column tile (column c of the
+// tile is transform c, element e is row ky = e).  Column 0 of the tile at
+// kx0 = 0 carries (DC, row-Nyquist) and is handled by (ky, -ky) pairs.
+// out may alias X0 (single term, in place: every thread writes only the
+// elements it read).
+template <typename real>
+__device__ __forceinline__ void col_multiply(typename cplx_of<real>::type *out, Lay lo,
+                                             const typename cplx_of<real>::type *X0, Lay l0,
+                                             const typename cplx_of<real>::type *X1, Lay l1, const GroupDesc &g,
+                                             int o, const real *kxt, const real *kyt, int kx0, int TW, int ny, int h,
+                                             real scale, int nthr) {
+    using C = typename cplx_of<real>::type;
+    const bool two = g.nterm[o] > 1;
+    const C *t0 = g.term_in[o][0] ? X1 : X0;
+    const Lay m0 = g.term_in[o][0] ? l1 : l0;
+    const C *t1 = g.term_in[o][1] ? X1 : X0;
+    const Lay m1 = g.term_in[o][1] ? l1 : l0;
+    const real p0 = (real)g.c[o][0][0], p1 = (real)g.c[o][0][1], p2 = (real)g.c[o][0][2], p3 = (real)g.c[o][0][3],
+               p4 = (real)g.c[o][0][4];
+    const real q0 = (real)g.c[o][1][0], q1 = (real)g.c[o][1][1], q2 = (real)g.c[o][1][2], q3 = (real)g.c[o][1][3],
+               q4 = (real)g.c[o][1][4];
+    const int tile = TW * ny;
+    for (int idx = threadIdx.x; idx < tile; idx += nthr) {
+        const int e = idx / TW, c = idx - e * TW;
+        const int kx = kx0 + c;
+        if (kx == 0) continue;
+        const real ax = kxt[kx], ay = kyt[e];
+        C acc = mult_apply<real>(p0, p1, p2, p3, p4, ax, ay, t0[m0(c, e)]);
+        if (two) acc = cadd(acc, mult_apply<real>(q0, q1, q2, q3, q4, ax, ay, t1[m1(c, e)]));
+        out[lo(c, e)] = cscale(acc, scale);
+    }
+    if (kx0 == 0) {
+        const real a0 = kxt[0], aN = kxt[h];
+        for (int j = threadIdx.x; j <= ny / 2; j += nthr) {
+            const int jm = (ny - j) % ny;
+            const real ay = kyt[j], aym = kyt[jm];
+            C outj, outm;
+            {
+                const C p = t0[m0(0, j)], q = t0[m0(0, jm)];
+                const C A = cscale(cadd(p, cconj(q)), real(0.5));
+                const C Bv = cscale(cmul_mi(csub(p, cconj(q))), real(0.5));
+                outj = cadd(mult_apply<real>(p0, p1, p2, p3, p4, a0, ay, A),
+                            cmul_i(mult_apply<real>(p0, p1, p2, p3, p4, aN, ay, Bv)));
+                outm = cadd(mult_apply<real>(p0, p1, p2, p3, p4, a0, aym, cconj(A)),
+                            cmul_i(mult_apply<real>(p0, p1, p2, p3, p4, aN, aym, cconj(Bv))));
+            }
+            if (two) {
+                const C p = t1[m1(0, j)], q = t1[m1(0, jm)];
+                const C A = cscale(cadd(p, cconj(q)), real(0.5));
+                const C Bv = cscale(cmul_mi(csub(p, cconj(q))), real(0.5));
+                outj = cadd(outj, cadd(mult_apply<real>(q0, q1, q2, q3, q4, a0, ay, A),
+                                       cmul_i(mult_apply<real>(q0, q1, q2, q3, q4, aN, ay, Bv))));
+                outm = cadd(outm, cadd(mult_apply<real>(q0, q1, q2, q3, q4, a0, aym, cconj(A)),
+                                       cmul_i(mult_apply<real>(q0, q1, q2, q3, q4, aN, aym, cconj(Bv)))));
+            }
+            out[lo(0, j)] = cscale(outj, scale);
+            if (jm != j) out[lo(0, jm)] = cscale(outm, scale);
+        }
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDesc *groups, int k, int ntiles,
+                                           int TW, int ny, int BOXR, const CUtensorMap *tmap) {
+    const int job = (int)blockIdx.x + k * (int)gridDim.x;
+    const int g = job / ntiles, t = job - g * ntiles;
+    const GroupDesc *G = groups + g;
+    const int nin = G->nin;
+    const int tile = TW * ny;
+    mbar_expect_tx(bar, (uint32_t)(nin * tile * sizeof(C)));
+    for (int s = 0; s < nin; ++s) {
+        const int sl = G->in_slot[s];
+        for (int r0 = 0; r0 < ny; r0 += BOXR)
+            tma_load_2d(dst + (size_t)s * tile + (size_t)r0 * TW, tmap, 2 * t * TW, sl * ny + r0, bar);
+    }
+}
+
+// MULTI = false: every group has one input and one output in place
+// (convection); MULTI = true: up to 2 inputs and several outputs.
+template <typename real, bool MULTI>
+__global__ void __launch_bounds__(KCfg<real>::NT, 1) kcol_pipe(typename cplx_of<real>::type *spec,
+                                                               const GroupDesc *__restrict__ groups, int ngroups,
+                                                               const real *__restrict__ kxt,
+                                                               const real *__restrict__ kyt,
+                                                               const typename cplx_of<real>::type *__restrict__ Wc_g,
+                                                               KP<real> P, int TW, int BOXR,
+                                                               const __grid_constant__ CUtensorMap tmap, int *err) {
+    using C = typename cplx_of<real>::type;
+    constexpr int NT = KCfg<real>::NT;
+    constexpr int NIN = MULTI ? 2 : 1;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1;
+    __shared__ GroupDesc gd;
+    const int ny = P.ny, h = P.h, tid = threadIdx.x;
+    const size_t slot = (size_t)ny * h;
+    const int tile = TW * ny;
+    const int ptile = TW * padded_len(ny);
+    SmemCursor sc{smem_raw, 0u};
+    C *Wc = (C *)sc.take(ny * sizeof(C));
+    C *buf0 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
+    C *buf1 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
+    C *wk0 = (C *)sc.take((size_t)ptile * sizeof(C));
+    C *wk1 = MULTI ? (C *)sc.take((size_t)ptile * sizeof(C)) : nullptr;
+    const Lay lt{1, TW, 0}, lw{1, TW, 1};   // staged tile / padded work tile
+    const int ntiles = h / TW;
+    const int njobs_total = ngroups * ntiles;
+    const int njobs = (int)blockIdx.x < njobs_total ? (njobs_total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(Wc, Wc_g, ny, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, TW, ny, BOXR, &tmap);
+        if (njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, TW, ny, BOXR, &tmap);
+    }
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = njobs > 0, pend1 = njobs > 1;
+    const real scale = P.scale;
+    for (int k = 0; k < njobs; ++k) {
+        const bool odd = k & 1;
+        uint64_t *bar = odd ? &bar1 : &bar0;
+        const int job = (int)blockIdx.x + k * (int)gridDim.x;
+        const int g = job / ntiles, t = job - g * ntiles;
+        const int kx0 = t * TW;
+        if (tid == 0) gd = groups[g];
+        if (!block_wait(bar, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        C *in0 = odd ? buf1 : buf0;
+        C *gout;
+        if (!MULTI) {
+            // convection: forward, multiply in place, inverse, store
+            const int w1 = pp_fft<-1, true>(in0, lt, wk0, lw, ny, TW, Wc, tid, NT);
+            C *X = w1 ? wk0 : in0;
+            C *Y = w1 ? in0 : wk0;
+            const Lay lx = w1 ? lw : lt, ly = w1 ? lt : lw;
+            col_multiply<real>(X, lx, X, lx, X, lx, gd, 0, kxt, kyt, kx0, TW, ny, h, scale, NT);
+            __syncthreads();
+            const int w2 = pp_fft<+1, true>(X, lx, Y, ly, ny, TW, Wc, tid, NT);
+            const C *R = w2 ? Y : X;
+            const Lay lr = w2 ? ly : lx;
+            gout = spec + (size_t)gd.out_slot[0] * slot + kx0;
+            for (int idx = tid; idx < tile; idx += NT) {
+                const int e = idx / TW, c = idx - e * TW;
+                gout[(size_t)e * h + c] = R[lr(c, e)];
+            }
+        } else {
+            // X0 in {in0, wk0}, X1 in {in1, wk1}; outputs ping-pong between
+            // the two buffers left free
+            C *in1 = in0 + tile;
+            const int w0 = pp_fft<-1, true>(in0, lt, wk0, lw, ny, TW, Wc, tid, NT);
+            C *X0 = w0 ? wk0 : in0;
+            C *F0 = w0 ? in0 : wk0;
+            const Lay lx0 = w0 ? lw : lt, lf0 = w0 ? lt : lw;
+            C *X1 = in1, *F1 = wk1;
+            Lay lx1 = lt, lf1 = lw;
+            if (gd.nin > 1) {
+                const int w1 = pp_fft<-1, true>(in1, lt, wk1, lw, ny, TW, Wc, tid, NT);
+                X1 = w1 ? wk1 : in1;
+                F1 = w1 ? in1 : wk1;
+                lx1 = w1 ? lw : lt;
+                lf1 = w1 ? lt : lw;
+            }
+            for (int o = 0; o < gd.nout; ++o) {
+                col_multiply<real>(F0, lf0, X0, lx0, X1, lx1, gd, o, kxt, kyt, kx0, TW, ny, h, scale, NT);
+                __syncthreads();
+                const int w2 = pp_fft<+1, true>(F0, lf0, F1, lf1, ny, TW, Wc, tid, NT);
+                const C *R = w2 ? F1 : F0;
+                const Lay lr = w2 ? lf1 : lf0;
+                gout = spec + (size_t)gd.out_slot[o] * slot + kx0;
+                for (int idx = tid; idx < tile; idx += NT) {
+                    const int e = idx / TW, c = idx - e * TW;
+                    gout[(size_t)e * h + c] = R[lr(c, e)];
+                }
+                __syncthreads();
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && k + 2 < njobs) {
+            kcol_issue(in0, bar, groups, k + 2, ntiles, TW, ny, BOXR, &tmap);
+            if (odd) pend1 = true;
+            else pend0 = true;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: level-1 derivatives -> Lambda, Phi, C / B numerators -> forward rows
+// ---------------------------------------------------------------------------
+
+constexpr int NT3 = 256;
+
+template <typename real>
+__global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spec, const real *__restrict__ fields,
+                                               real *__restrict__ aux,
+                                               const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                               const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P,
+                                               int WR, int *err) {
+    using C = typename cplx_of<real>::type;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    const int ph = padded_len(h);
+    SmemCursor sc{smem_raw, 0u};
+    C *Wr = (C *)sc.take(h * sizeof(C));
+    C *Wp = (C *)sc.take(h * sizeof(C));
+    C *d = (C *)sc.take((size_t)ND1 * h * sizeof(C));
+    C *wk = (C *)sc.take((size_t)WR * ph * sizeof(C));
+    real *rT = (real *)sc.take((size_t)2 * nx * sizeof(real));
+    const Lay la{h, 1, 0}, lb{ph, 1, 1};
+    const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        mbar_expect_tx(&bar, (uint32_t)(ND1 + 2) * rowbytes);
+        for (int o = 0; o < ND1; ++o)
+            bulk_g2s(d + (size_t)o * h, spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h, rowbytes, &bar);
+        bulk_g2s(rT, fields + (size_t)y * nx, rowbytes, &bar);
+        bulk_g2s(rT + nx, fields + 3 * N + (size_t)y * nx, rowbytes, &bar);
+    }
+    load_tab(Wr, Wr_g, h, NT3);
+    load_tab(Wp, Wp_g, h, NT3);
+    if (!block_wait(&bar, 0, err)) {
+        mbar_wait_bounded(&bar, 0);
+        return;
+    }
+    c2r_pre_l(d, la, h, ND1, Wp, tid, NT3);
+    __syncthreads();
+    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, NT3);
+    const C *res = d;
+    const Lay lr = la;
+    real *dw = reinterpret_cast<real *>(d);
+    for (int x = tid; x < nx; x += NT3) {
+        const size_t s = (size_t)y * nx + x;
+        const real rho = rT[x], T = rT[nx + x];
+        const real rx = real_at<real>(res, lr, D_RX, x), ry = real_at<real>(res, lr, D_RY, x);
+        const real lap = real_at<real>(res, lr, D_LAP, x);
+        const real uxx = real_at<real>(res, lr, D_UXX, x), uxy = real_at<real>(res, lr, D_UXY, x);
+        const real uyx = real_at<real>(res, lr, D_UYX, x), uyy = real_at<real>(res, lr, D_UYY, x);
+        const real divx = real_at<real>(res, lr, D_DIVX, x), divy = real_at<real>(res, lr, D_DIVY, x);
+        const real Tx = real_at<real>(res, lr, D_TX, x), Ty = real_at<real>(res, lr, D_TY, x);
+        const real Pix = real_at<real>(res, lr, D_PIX, x), Piy = real_at<real>(res, lr, D_PIY, x);
+        const real gx = real_at<real>(res, lr, D_GX, x), gy = real_at<real>(res, lr, D_GY, x);
+        const real M = P.K + P.H * T;
+        const real Pi = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;
+        const real grad2 = rx * rx + ry * ry;
+        const real iso = -(rho * T * (rx * gx + ry * gy)) - M * (rho * lap + real(0.5) * grad2);   // Eq. 19
+        const real Lxx = M * rx * rx + iso, Lxy = M * rx * ry, Lyy = M * ry * ry + iso;
+        const real div = uxx + uyy;
+        const real Ldu = Lxx * uxx + Lxy * (uyx + uxy) + Lyy * uyy;
+        const real Cn = Pi * div + Ldu - P.zeta * div * div + P.a * rho * rho * div +
+                        P.K * (real(-0.5) * grad2 * div - rho * (rx * divx + ry * divy) -
+                               (rx * (uxx * rx + uyx * ry) + ry * (uxy * rx + uyy * ry)));   // Eq. 22
+        aux[s] = Cn;
+        aux[N + s] = Pix - P.zeta * divx;   // Eq. 21 without d_b Lambda_ab
+        aux[2 * N + s] = Piy - P.zeta * divy;
+        const real q2 = real(2) * P.q * rho * T;   // Eq. 23
+        // rows 0..4 of d (same site, same thread)
+        dw[0 * nx + x] = Lxx;
+        dw[1 * nx + x] = Lxy;
+        dw[2 * nx + x] = Lyy;
+        dw[3 * nx + x] = q2 * Tx;
+        dw[4 * nx + x] = q2 * Ty;
+    }
+    __syncthreads();
+    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, NT3);
+    C *res2 = d;
+    const Lay lr2 = la;
+    r2c_post_l(res2, lr2, h, 5, Wp, tid, NT3);
+    __syncthreads();
+    for (int r = 0; r < 5; ++r) {
+        C *dst = spec + (size_t)(SLOT_L2 + r) * slot + (size_t)y * h;
+        for (int k = tid; k < h; k += NT3) dst[k] = res2[lr2(r, k)];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: convection + level-2 -> coefficients -> f^eq, I, BGK, RK combination
+// ---------------------------------------------------------------------------
+
+constexpr int CHMAX5 = 8;
+constexpr int NHEAD = 10;   // dLx, dLy, dPhi spectra; rho, ux, uy, T; Cn, Bnx, Bny
+
+template <typename real>
+__device__ __forceinline__ void k5_issue_chunk(const typename cplx_of<real>::type *spec, real *dst, uint64_t *bar,
+                                               int j, int nchunk, int CH, int nx, size_t slot, int h) {
+    const int ri = j / nchunk, c = j - ri * nchunk;
+    const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int v0 = c * CH, nv = min(CH, NMOV - v0);
+    const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
+    mbar_expect_tx(bar, (uint32_t)nv * rowbytes);
+    for (int r = 0; r < nv; ++r)
+        bulk_g2s(dst + (size_t)r * nx, spec + (size_t)(v0 + r) * slot + (size_t)y * h, rowbytes, bar);
+}
+
+template <typename real>
+__device__ __forceinline__ void k5_issue_head(const typename cplx_of<real>::type *spec, const real *fields,
+                                              const real *aux, real *dst, uint64_t *bar, int ri, int nx, size_t N,
+                                              size_t slot, int h) {
+    const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+    const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
+    mbar_expect_tx(bar, (uint32_t)NHEAD * rowbytes);
+    bulk_g2s(dst, spec + (size_t)(SLOT_L2 + 0) * slot + (size_t)y * h, rowbytes, bar);
+    bulk_g2s(dst + nx, spec + (size_t)(SLOT_L2 + 2) * slot + (size_t)y * h, rowbytes, bar);
+    bulk_g2s(dst + 2 * (size_t)nx, spec + (size_t)(SLOT_L2 + 3) * slot + (size_t)y * h, rowbytes, bar);
+    for (int r = 0; r < 4; ++r)
+        bulk_g2s(dst + (size_t)(3 + r) * nx, fields + (size_t)r * N + (size_t)y * nx, rowbytes, bar);
+    for (int r = 0; r < 3; ++r)
+        bulk_g2s(dst + (size_t)(7 + r) * nx, aux + (size_t)r * N + (size_t)y * nx, rowbytes, bar);
+}
+
+// NHB head buffers (1 or 2): the head of row ri lives in buffer ri % NHB and
+// is prefetched NHB rows ahead.
+template <typename real, int SMAX>
+__global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx_of<real>::type *spec,
+                                                             const real *__restrict__ fields,
+                                                             const real *__restrict__ aux, const real *fcur,
+                                                             const real *fbase, real *fout, real alpha, real beta,
+                                                             const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                             const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                             KP<real> P, int CH, int NHB, int *err) {
+    using C = typename cplx_of<real>::type;
+    constexpr int NT = KCfg<real>::NT;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1, hbar0, hbar1;
+    const int nx = P.nx, ny = P.ny, h = P.h, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    const int ph = padded_len(h);
+    SmemCursor sc{smem_raw, 0u};
+    C *Wr = (C *)sc.take(h * sizeof(C));
+    C *Wp = (C *)sc.take(h * sizeof(C));
+    real *head0 = (real *)sc.take((size_t)NHEAD * nx * sizeof(real));
+    real *head1 = NHB > 1 ? (real *)sc.take((size_t)NHEAD * nx * sizeof(real)) : head0;
+    real *buf0 = (real *)sc.take((size_t)CH * nx * sizeof(real));
+    real *buf1 = (real *)sc.take((size_t)CH * nx * sizeof(real));
+    C *wk = (C *)sc.take((size_t)max(CH, 3) * ph * sizeof(C));
+    const Lay la{h, 1, 0}, lb{ph, 1, 1};
+    const int nchunk = (NMOV + CH - 1) / CH;
+    const int nrows = (int)blockIdx.x < ny ? (ny - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs = nrows * nchunk;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init(&hbar0, 1);
+        mbar_init(&hbar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(Wr, Wr_g, h, NT);
+    load_tab(Wp, Wp_g, h, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, N, slot, h);
+        if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, N, slot, h);
+        if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, nchunk, CH, nx, slot, h);
+        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, nchunk, CH, nx, slot, h);
+    }
+    uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
+    bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
+    const real dt = P.dt, itau = real(1) / P.tau;
+    const bool with_base = alpha != real(0);
+    for (int j = 0; j < njobs; ++j) {
+        const bool odd = j & 1;
+        const int ri = j / nchunk, c = j - ri * nchunk;
+        const bool hodd = (NHB > 1) && (ri & 1);
+        const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int v0 = c * CH, nv = min(CH, NMOV - v0);
+        real *H = hodd ? head1 : head0;
+        if (c == 0) {
+            if (!block_wait(hodd ? &hbar1 : &hbar0, hodd ? hpar1 : hpar0, err)) {
+                if (pend0) mbar_wait_bounded(&bar0, par0);
+                if (pend1) mbar_wait_bounded(&bar1, par1);
+                if (hpend0) mbar_wait_bounded(&hbar0, hpar0);
+                if (hpend1) mbar_wait_bounded(&hbar1, hpar1);
+                return;
+            }
+            if (hodd) {
+                hpar1 ^= 1;
+                hpend1 = false;
+            } else {
+                hpar0 ^= 1;
+                hpend0 = false;
+            }
+            C *l2 = reinterpret_cast<C *>(H);
+            c2r_pre_l(l2, la, h, 3, Wp, tid, NT);
+            __syncthreads();
+            const int w = pp_fft<+1, false>(l2, la, wk, lb, h, 3, Wr, tid, NT);
+            const C *lres = w ? wk : l2;
+            const Lay llr = w ? lb : la;
+            // per-site coefficients, written over the head rows (same site,
+            // same thread): row 0 <- e0, 1 <- e1x, 2 <- e1y, 7 <- C + C_q
+#pragma unroll 1
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x < nx) {
+                    const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
+                    const real dLx = real_at<real>(lres, llr, 0, x), dLy = real_at<real>(lres, llr, 1, x);
+                    const real dPh = real_at<real>(lres, llr, 2, x);
+                    const real rT = rho * T;
+                    const real inv2 = real(1) / (real(2) * rho * T * T);
+                    const real Bx = (H[8 * nx + x] + dLx) / rT;      // Eq. 21
+                    const real By = (H[9 * nx + x] + dLy) / rT;
+                    const real CC = (H[7 * nx + x] + dPh) * inv2;    // C + C_q, Eqs. 22-23
+                    const real A = real(-2) * CC * T;                // Eq. 20
+                    const real u2 = ux * ux + uy * uy;
+                    // I = -(A + B.(v-u) + CC |v-u|^2) f^eq = -(e0 + e1.v + CC |v|^2) f^eq
+                    const real e0 = A - (Bx * ux + By * uy) + CC * u2;
+                    H[x] = e0;
+                    H[nx + x] = Bx - real(2) * CC * ux;
+                    H[2 * nx + x] = By - real(2) * CC * uy;
+                    H[7 * nx + x] = CC;
+                    // rest velocity (no convection)
+                    real F[5];
+                    weights_Fk<real>(T, F);
+                    const real qq = real(0.5) * u2 / T, om = real(1) - qq;
+                    const real fe = rho * F[0] * (om + real(0.5) * qq * qq);
+                    const size_t o = (size_t)y * nx + x;
+                    const real fc = fcur[o];
+                    real fn = beta * (fc + dt * (-(fc - fe) * itau - e0 * fe));
+                    if (with_base) fn += alpha * fbase[o];
+                    fout[o] = fn;
+                }
+            }
+            __syncthreads();
+        }
+        if (!block_wait(odd ? &bar1 : &bar0, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            if (hpend0) mbar_wait_bounded(&hbar0, hpar0);
+            if (hpend1) mbar_wait_bounded(&hbar1, hpar1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        real *B = odd ? buf1 : buf0;
+        C *Bc = reinterpret_cast<C *>(B);
+        c2r_pre_l(Bc, la, h, nv, Wp, tid, NT);
+        __syncthreads();
+        const int w = pp_fft<+1, false>(Bc, la, wk, lb, h, nv, Wr, tid, NT);
+        const C *cres = w ? wk : Bc;
+        const Lay lcr = w ? lb : la;
+#pragma unroll 1
+        for (int s = 0; s < SMAX; ++s) {
+            const int x = tid + s * NT;
+            if (x >= nx) continue;
+            real fc[CHMAX5], fb[CHMAX5];
+#pragma unroll
+            for (int r = 0; r < CHMAX5; ++r) {
+                if (r < nv) {
+                    const size_t o = (size_t)(1 + v0 + r) * N + (size_t)y * nx + x;
+                    fc[r] = fcur[o];
+                    fb[r] = with_base ? fbase[o] : real(0);
+                }
+            }
+            const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
+            const real e0 = H[x], e1x = H[nx + x], e1y = H[2 * nx + x], CC = H[7 * nx + x];
+            real F[5];
+            weights_Fk<real>(T, F);                                  // Eqs. 4-6
+            const real iT = real(1) / T, qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
+            const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
+            const real p3 = iT * iT * iT / real(6), p4 = iT * iT * iT * iT / real(24);
+#pragma unroll
+            for (int r = 0; r < CHMAX5; ++r) {
+                if (r < nv) {
+                    const int i = 1 + v0 + r;
+                    const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
+                    const int k = c_ring[i];
+                    const real vu = vx * ux + vy * uy;
+                    const real br = p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4)));
+                    real rF = F[1];
+                    rF = (k == 2) ? F[2] : rF;
+                    rF = (k == 3) ? F[3] : rF;
+                    rF = (k == 4) ? F[4] : rF;
+                    const real fe = rho * rF * br;                                          // Eq. 3
+                    const real I = -(e0 + e1x * vx + e1y * vy + CC * v2) * fe;              // Eq. 11
+                    const real conv = real_at<real>(cres, lcr, r, x);
+                    const real rhs = -conv - (fc[r] - fe) * itau + I;                       // Eq. 10
+                    real fn = beta * (fc[r] + dt * rhs);
+                    if (with_base) fn += alpha * fb[r];
+                    fout[(size_t)i * N + (size_t)y * nx + x] = fn;
+                }
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            if (j + 2 < njobs) {
+                k5_issue_chunk<real>(spec, B, odd ? &bar1 : &bar0, j + 2, nchunk, CH, nx, slot, h);
+                if (odd) pend1 = true;
+                else pend0 = true;
+            }
+            // the row's head buffer is free after its last chunk: prefetch
+            // the head of row ri + NHB into it
+            if (c == nchunk - 1 && ri + NHB < nrows) {
+                k5_issue_head<real>(spec, fields, aux, H, hodd ? &hbar1 : &hbar0, ri + NHB, nx, N, slot, h);
+                if (hodd) hpend1 = true;
+                else hpend0 = true;
+            }
+        }
+    }
+}
+
+}  // namespace fftlb
