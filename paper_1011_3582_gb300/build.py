@@ -2,7 +2,10 @@
 
 Every translation unit is compiled in parallel with nvcc, then linked into a
 shared library next to this file.  Rebuilds only when a source is newer than
-the library (or when force=True).
+the library, when the extra flags changed, or when force=True.
+
+FFTLB_NVCC_FLAGS (environment) adds nvcc flags, e.g. the launch-shape knobs
+of csrc/kernels_pipe.cuh: -DFFTLB_NT32=256 -DFFTLB_MINB32=2.
 """
 from __future__ import annotations
 
@@ -18,6 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfftlb.so")
+STAMP = os.path.join(BUILD, "flags.txt")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -40,8 +44,15 @@ def deps():
         + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date():
+def env_flags():
+    return os.environ.get("FFTLB_NVCC_FLAGS", "").split()
+
+
+def up_to_date(extra=()):
     if not os.path.exists(LIB):
+        return False
+    want = " ".join(list(extra) + env_flags())
+    if not os.path.exists(STAMP) or open(STAMP).read() != want:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in deps())
@@ -57,10 +68,10 @@ def _compile(src, extra):
 
 
 def build(force=False, verbose=False, extra=()):
-    if not force and up_to_date():
+    if not force and up_to_date(extra):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra)
+    extra = list(extra) + env_flags()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), sources()))
     objs = [o for o, _ in results]
@@ -74,6 +85,8 @@ def build(force=False, verbose=False, extra=()):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(extra))
     return LIB
 
 

@@ -885,6 +885,8 @@ class EngineT : public Engine {
     C *spec_ = nullptr;
     real *kxt_ = nullptr, *kyt_ = nullptr;
     C *Wr_ = nullptr, *Wp_ = nullptr, *Wc_ = nullptr;
+    C *Tr_ = nullptr, *Tc_ = nullptr;   // pass twiddle tables (power-of-two lengths)
+    int ntr_ = 0, ntc_ = 0;
     GroupDesc *groups_ = nullptr;
     double *partial_ = nullptr, *red_ = nullptr;
     void *scratch_d_ = nullptr;
@@ -1116,6 +1118,33 @@ class EngineT : public Engine {
         }
     }
 
+    // per-pass twiddle tables of the power-of-two passes (see
+    // pass_twiddle_len): T[t Ns + k] = exp(-2 pi i t k / (Ns R))
+    static void pass_twiddles(std::vector<C> &T, int n) {
+        T.clear();
+        if (!is_pow2(n)) return;
+        const long double pi = 3.141592653589793238462643383279502884L;
+        int logn = 0;
+        while ((1 << logn) < n) ++logn;
+        int logNs = 0, rem = logn;
+        while (rem > 0) {
+            const int lr = rem >= 4 ? 4 : rem;
+            if (logNs > 0) {
+                const int Ns = 1 << logNs, R = 1 << lr;
+                for (int t = 0; t < R; ++t)
+                    for (int k = 0; k < Ns; ++k) {
+                        const long double a = 2.0L * pi * (long double)(t * k) / (long double)(Ns * R);
+                        C w;
+                        w.x = (real)cosl(a);
+                        w.y = (real)(-sinl(a));
+                        T.push_back(w);
+                    }
+            }
+            logNs += lr;
+            rem -= lr;
+        }
+    }
+
     Status build_tables() {
         std::vector<real> kx(h_ + 1), ky(ny_);
         for (int j = 0; j <= h_; ++j) kx[j] = (real)kappa(j, nx_);   // j = h is the Nyquist bin
@@ -1129,6 +1158,16 @@ class EngineT : public Engine {
         FFTLB_CU(cudaMemcpy(Wr_, wr.data(), wr.size() * sizeof(C), cudaMemcpyHostToDevice));
         FFTLB_CU(cudaMemcpy(Wp_, wp.data(), wp.size() * sizeof(C), cudaMemcpyHostToDevice));
         FFTLB_CU(cudaMemcpy(Wc_, wc.data(), wc.size() * sizeof(C), cudaMemcpyHostToDevice));
+        std::vector<C> tr, tc;
+        pass_twiddles(tr, h_);
+        pass_twiddles(tc, ny_);
+        ntr_ = (int)tr.size();
+        ntc_ = (int)tc.size();
+        Status st;
+        if (!(st = dalloc(&Tr_, std::max<size_t>(1, tr.size()))).good()) return st;
+        if (!(st = dalloc(&Tc_, std::max<size_t>(1, tc.size()))).good()) return st;
+        if (ntr_) FFTLB_CU(cudaMemcpy(Tr_, tr.data(), tr.size() * sizeof(C), cudaMemcpyHostToDevice));
+        if (ntc_) FFTLB_CU(cudaMemcpy(Tc_, tc.data(), tc.size() * sizeof(C), cudaMemcpyHostToDevice));
         return Status::ok();
     }
 
@@ -1339,23 +1378,34 @@ class EngineT : public Engine {
         SMAX1_ = (nx_ + NT - 1) / NT;
         SMAX1_ = SMAX1_ <= 1 ? 1 : (SMAX1_ <= 2 ? 2 : 4);
         SMAX5_ = SMAX1_;
-        // K1: chunks of 6..8 rows (>= 6 for the level-1 rows)
-        CH1_ = 0;
-        for (int ch = 8; ch >= 6; --ch) {
-            const size_t sm = smem_bytes({h_ * cs, h_ * cs, (size_t)ch * nx_ * rs, (size_t)ch * nx_ * rs, ch * ph * cs});
-            if (sm <= budget) {
-                CH1_ = ch;
-                smem1_ = sm;
-                break;
+        // K1: chunks of 6..8 rows (>= 6 for the level-1 rows); most blocks
+        // per SM first, then the largest chunk
+        {
+            int bestnb = 0;
+            CH1_ = 0;
+            for (int ch = 8; ch >= 6; --ch) {
+                const size_t sm =
+                    smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ch * nx_ * rs, (size_t)ch * nx_ * rs, ch * ph * cs});
+                if (sm > budget) continue;
+                if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, sm, &nb);
+                else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, sm, &nb);
+                else st = occupancy(k1_pipe<real, 4>, NT, sm, &nb);
+                if (!st.good()) return st;
+                if (nb > bestnb) {
+                    bestnb = nb;
+                    CH1_ = ch;
+                    smem1_ = sm;
+                }
             }
+            if (!CH1_) return Status::err(FFTLB_ERR_ARG, "grid too large for the row kernel");
+            if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, smem1_, &nb);
+            else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, smem1_, &nb);
+            else st = occupancy(k1_pipe<real, 4>, NT, smem1_, &nb);
+            if (!st.good()) return st;
+            grid1_ = std::min(ny_, std::max(1, nb) * nsm_);
         }
-        if (!CH1_) return Status::err(FFTLB_ERR_ARG, "grid too large for the row kernel");
-        if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, smem1_, &nb);
-        else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, smem1_, &nb);
-        else st = occupancy(k1_pipe<real, 4>, NT, smem1_, &nb);
-        if (!st.good()) return st;
-        grid1_ = std::min(ny_, std::max(1, nb) * nsm_);
-        // column kernels: box height divides ny; widest tile that fits
+        // column kernels: box height divides ny; most blocks per SM first,
+        // then the widest tile
         BOXR_ = 1;
         for (int d = std::min(ny_, 256); d >= 1; --d)
             if (ny_ % d == 0) {
@@ -1363,32 +1413,41 @@ class EngineT : public Engine {
                 break;
             }
         const size_t pny = (size_t)padded_len(ny_);
-        auto pick_tw = [&](bool multi, int *tw_out, size_t *sm_out) -> bool {
+        auto pick_tw = [&](bool multi, int *tw_out, size_t *sm_out, int *grid_out) -> Status {
+            int bestnb = 0;
+            *tw_out = 0;
             for (int tw = 8; tw >= 1; tw >>= 1) {
                 if (h_ % tw) continue;
                 if ((2 * tw * rs) % 16) continue;   // tensor box row: whole 16-byte units
                 const size_t tile = (size_t)tw * ny_ * cs, ptile = (size_t)tw * pny * cs;
-                const size_t sm = multi ? smem_bytes({ny_ * cs, 2 * tile, 2 * tile, ptile, ptile})
-                                        : smem_bytes({ny_ * cs, tile, tile, ptile});
+                const size_t kt = (h_ + 1 + ny_) * rs;
+                const size_t sm = multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, 2 * tile, 2 * tile, ptile, ptile})
+                                        : smem_bytes({ny_ * cs, ntc_ * cs, kt, tile, tile, ptile});
                 if (sm > budget) continue;
-                *tw_out = tw;
-                *sm_out = sm;
-                return true;
+                Status s2 = multi ? occupancy(kcol_pipe<real, true>, NT, sm, &nb)
+                                  : occupancy(kcol_pipe<real, false>, NT, sm, &nb);
+                if (!s2.good()) return s2;
+                if (nb > bestnb) {
+                    bestnb = nb;
+                    *tw_out = tw;
+                    *sm_out = sm;
+                }
             }
-            return false;
+            if (!*tw_out) return Status::err(FFTLB_ERR_ARG, "grid too large for the column kernel");
+            Status s3 = multi ? occupancy(kcol_pipe<real, true>, NT, *sm_out, &nb)
+                              : occupancy(kcol_pipe<real, false>, NT, *sm_out, &nb);
+            *grid_out = std::max(1, nb) * nsm_;
+            return s3;
         };
-        if (!pick_tw(false, &TWc_, &smemc_) || !pick_tw(true, &TWl_, &smeml_))
-            return Status::err(FFTLB_ERR_ARG, "grid too large for the column kernel");
-        if (!(st = occupancy(kcol_pipe<real, false>, NT, smemc_, &nb)).good()) return st;
-        gridc_ = std::max(1, nb) * nsm_;
-        if (!(st = occupancy(kcol_pipe<real, true>, NT, smeml_, &nb)).good()) return st;
-        gridl_ = std::max(1, nb) * nsm_;
+        if (!(st = pick_tw(false, &TWc_, &smemc_, &gridc_)).good()) return st;
+        if (!(st = pick_tw(true, &TWl_, &smeml_, &gridl_)).good()) return st;
         if (!(st = make_tmap(&tmap_conv_, TWc_)).good()) return st;
         if (!(st = make_tmap(&tmap_l1_, TWl_)).good()) return st;
         // K3
         WR3_ = 0;
         for (int wr = ND1; wr >= 1; --wr) {
-            smem3_ = smem_bytes({h_ * cs, h_ * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs, (size_t)2 * nx_ * rs});
+            smem3_ = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs,
+                                 (size_t)2 * nx_ * rs});
             if (smem3_ <= budget) {
                 WR3_ = wr;
                 break;
@@ -1396,19 +1455,29 @@ class EngineT : public Engine {
         }
         if (!WR3_) return Status::err(FFTLB_ERR_ARG, "grid too large for the level-1 row kernel");
         if (!(st = occupancy(k3_pipe<real>, NT3, smem3_, &nb)).good()) return st;
-        // K5: two head buffers when they fit, chunks of up to 8 rows
-        CH5_ = 0;
-        for (int nhb = 2; nhb >= 1 && !CH5_; --nhb) {
-            for (int ch = CHMAX5; ch >= 2; ch -= 2) {
-                const size_t head = (size_t)NHEAD * nx_ * rs;
-                const size_t sm =
-                    smem_bytes({h_ * cs, h_ * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
-                                (size_t)ch * nx_ * rs, (size_t)std::max(ch, 3) * ph * cs});
-                if (sm <= budget && (ch >= 4 || nhb == 1)) {
-                    CH5_ = ch;
-                    NHB5_ = nhb;
-                    smem5_ = sm;
-                    break;
+        // K5: most blocks per SM first, then two head buffers, then the
+        // largest chunk
+        {
+            int bestscore = -1;
+            CH5_ = 0;
+            for (int nhb = 2; nhb >= 1; --nhb) {
+                for (int ch = CHMAX5; ch >= 2; ch -= 2) {
+                    const size_t head = (size_t)NHEAD * nx_ * rs;
+                    const size_t sm =
+                        smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
+                                    (size_t)ch * nx_ * rs, (size_t)std::max(ch, 3) * ph * cs});
+                    if (sm > budget) continue;
+                    if (SMAX5_ == 1) st = occupancy(k5_pipe<real, 1>, NT, sm, &nb);
+                    else if (SMAX5_ == 2) st = occupancy(k5_pipe<real, 2>, NT, sm, &nb);
+                    else st = occupancy(k5_pipe<real, 4>, NT, sm, &nb);
+                    if (!st.good()) return st;
+                    const int score = nb * 100 + nhb * 10 + ch;
+                    if (nb > 0 && score > bestscore) {
+                        bestscore = score;
+                        CH5_ = ch;
+                        NHB5_ = nhb;
+                        smem5_ = sm;
+                    }
                 }
             }
         }
@@ -1432,11 +1501,11 @@ class EngineT : public Engine {
     Status launch_col(int first, int count, bool level1) {
         if (level1)
             kcol_pipe<real, true><<<gridl_, KCfg<real>::NT, smeml_, stream_>>>(spec_, groups_ + first, count, kxt_,
-                                                                               kyt_, Wc_, kp_, TWl_, BOXR_, tmap_l1_,
-                                                                               err_);
+                                                                               kyt_, Wc_, Tc_, ntc_, kp_, TWl_, BOXR_,
+                                                                               tmap_l1_, err_);
         else
             kcol_pipe<real, false><<<gridc_, KCfg<real>::NT, smemc_, stream_>>>(
-                spec_, groups_ + first, count, kxt_, kyt_, Wc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
+                spec_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
         FFTLB_LAUNCHED("kcol_pipe");
         return Status::ok();
     }
@@ -1445,11 +1514,14 @@ class EngineT : public Engine {
         Status st;
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
         if (SMAX1_ == 1)
-            k1_pipe<real, 1><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, CH1_, err_);
+            k1_pipe<real, 1><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+                                                                                 CH1_, err_);
         else if (SMAX1_ == 2)
-            k1_pipe<real, 2><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, CH1_, err_);
+            k1_pipe<real, 2><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+                                                                                 CH1_, err_);
         else
-            k1_pipe<real, 4><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, kp_, CH1_, err_);
+            k1_pipe<real, 4><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+                                                                                 CH1_, err_);
         FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
@@ -1459,7 +1531,7 @@ class EngineT : public Engine {
         if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
-        k3_pipe<real><<<ny_, NT3, smem3_, stream_>>>(spec_, fields_, aux_, Wr_, Wp_, kp_, WR3_, err_);
+        k3_pipe<real><<<ny_, NT3, smem3_, stream_>>>(spec_, fields_, aux_, Wr_, Wp_, Tr_, ntr_, kp_, WR3_, err_);
         FFTLB_LAUNCHED("k3_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL2)).good()) return st;
@@ -1468,13 +1540,13 @@ class EngineT : public Engine {
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         if (SMAX5_ == 1)
             k5_pipe<real, 1><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, kp_, CH5_, NHB5_, err_);
+                                                               Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         else if (SMAX5_ == 2)
             k5_pipe<real, 2><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, kp_, CH5_, NHB5_, err_);
+                                                               Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         else
             k5_pipe<real, 4><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, kp_, CH5_, NHB5_, err_);
+                                                               Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         FFTLB_LAUNCHED("k5_pipe");
         return prof_end();
     }

@@ -25,6 +25,14 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+
+#ifndef FFTLB_NO_PACKED_F32X2
+// fp32 complex add / subtract as one packed FP32x2 instruction (sm_100+)
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+#endif
 // i * a and -i * a
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return C{-a.y, a.x}; }
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return C{a.y, -a.x}; }
@@ -94,45 +102,48 @@ template <int DIR, typename C> struct SmallDFT<8, DIR, C> {
     }
 };
 
-// z * exp(DIR i pi m / 8) for the products m = b k1 of the radix-16 split
-template <int DIR, typename C>
-__device__ __forceinline__ C mul_w16(C z, int m) {
-    using R = decltype(z.x);
-    const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);
-    const R h = R(0.70710678118654752440);
-    R wr, wi;
-    switch (m) {
-        case 0: return z;
-        case 1: wr = c1; wi = s1; break;
-        case 2: wr = h; wi = h; break;
-        case 3: wr = s1; wi = c1; break;
-        case 4: return (DIR < 0) ? cmul_mi(z) : cmul_i(z);
-        case 6: wr = -h; wi = h; break;
-        default: wr = -c1; wi = -s1; break;   // m = 9
-    }
-    wi = (DIR < 0) ? -wi : wi;
-    return cmul(z, C{wr, wi});
+// z * (wr + i DIR wi) for the constant twiddles of the radix-16 split
+template <int DIR, typename C, typename R>
+__device__ __forceinline__ C mul_wc(C z, R wr, R wi) {
+    const R s = (DIR < 0) ? -wi : wi;
+    return C{z.x * wr - z.y * s, z.x * s + z.y * wr};
 }
 
 // radix 16 as 4 x 4: z[b][k1] = DFT4_a x[4a + b]; z *= W16^(b k1);
-// y[k1 + 4 k2] = DFT4_b z[b][k1]
+// y[k1 + 4 k2] = DFT4_b z[b][k1].  The nine non-trivial W16^(b k1),
+// exp(DIR i pi m / 8) for m = b k1 in {1, 2, 3, 2, 4, 6, 3, 6, 9}, are
+// written out so that every factor is a compile-time constant.
 template <int DIR, typename C> struct SmallDFT<16, DIR, C> {
     __device__ __forceinline__ static void run(C *v) {
-        C z[4][4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) z[b][a] = v[4 * a + b];
-            SmallDFT<4, DIR, C>::run(z[b]);
-#pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1) z[b][k1] = mul_w16<DIR>(z[b][k1], b * k1);
-        }
+        using R = decltype(v[0].x);
+        const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);
+        const R h = R(0.70710678118654752440);
+        C z0[4] = {v[0], v[4], v[8], v[12]};
+        C z1[4] = {v[1], v[5], v[9], v[13]};
+        C z2[4] = {v[2], v[6], v[10], v[14]};
+        C z3[4] = {v[3], v[7], v[11], v[15]};
+        SmallDFT<4, DIR, C>::run(z0);
+        SmallDFT<4, DIR, C>::run(z1);
+        SmallDFT<4, DIR, C>::run(z2);
+        SmallDFT<4, DIR, C>::run(z3);
+        // b = 1: m = 1, 2, 3;  b = 2: m = 2, 4, 6;  b = 3: m = 3, 6, 9
+        z1[1] = mul_wc<DIR>(z1[1], c1, s1);
+        z1[2] = mul_wc<DIR>(z1[2], h, h);
+        z1[3] = mul_wc<DIR>(z1[3], s1, c1);
+        z2[1] = mul_wc<DIR>(z2[1], h, h);
+        z2[2] = (DIR < 0) ? cmul_mi(z2[2]) : cmul_i(z2[2]);
+        z2[3] = mul_wc<DIR>(z2[3], -h, h);
+        z3[1] = mul_wc<DIR>(z3[1], s1, c1);
+        z3[2] = mul_wc<DIR>(z3[2], -h, h);
+        z3[3] = mul_wc<DIR>(z3[3], -c1, -s1);
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
-            C t[4] = {z[0][k1], z[1][k1], z[2][k1], z[3][k1]};
+            C t[4] = {z0[k1], z1[k1], z2[k1], z3[k1]};
             SmallDFT<4, DIR, C>::run(t);
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+            v[k1] = t[0];
+            v[k1 + 4] = t[1];
+            v[k1 + 8] = t[2];
+            v[k1 + 12] = t[3];
         }
     }
 };
@@ -223,49 +234,178 @@ __device__ int pp_fft(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *W,
     return where;
 }
 
+__host__ __device__ inline int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+__host__ __device__ inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Power-of-two version of pp_pass: n, Ns and (with BFAST) nbatch are powers
+// of two, so the butterfly decomposition uses shifts and masks, and element
+// addresses advance by constant strides (the padded index e + e/16 is
+// linear in t whenever the stride n/R or Ns is a multiple of 16).
+template <int R, int DIR, bool BFAST, int PADS, int PADD, typename C>
+__device__ __forceinline__ void pp_pass_p2(const C *src, int sbs, int ses, C *dst, int dbs, int des, int logn,
+                                           int nbatch, int lognbatch, int logNs, const C *T, int tid, int nthr) {
+    constexpr int LR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    const int lognb = logn - LR;
+    const int nb = 1 << lognb;
+    const int Ns = 1 << logNs;
+    const int total = nbatch << lognb;
+    const bool rlin = !PADS || nb >= 16;
+    const bool wlin = !PADD || Ns >= 16;
+    const int rstep = (PADS ? nb + (nb >> 4) : nb) * ses;
+    const int wstep = (PADD ? Ns + (Ns >> 4) : Ns) * des;
+    for (int J = tid; J < total; J += nthr) {
+        int b, jj;
+        if (BFAST) {
+            b = J & (nbatch - 1);
+            jj = J >> lognbatch;
+        } else {
+            b = J >> lognb;
+            jj = J & (nb - 1);
+        }
+        const int k = jj & (Ns - 1);
+        const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
+        C v[R];
+        if (rlin) {
+            const C *p = src + b * sbs + (PADS ? jj + (jj >> 4) : jj) * ses;
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = p[t * rstep];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = jj + t * nb;
+                v[t] = src[b * sbs + (e + (e >> 4)) * ses];
+            }
+        }
+        if (Ns > 1) {
+            const C *tw = T + k;   // this pass's table: T[t Ns + k] = exp(-2 pi i t k / (Ns R))
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                C w = tw[t * Ns];
+                if (DIR > 0) w.y = -w.y;
+                v[t] = cmul(v[t], w);
+            }
+        }
+        SmallDFT<R, DIR, C>::run(v);
+        if (wlin) {
+            C *q = dst + b * dbs + (PADD ? idxD + (idxD >> 4) : idxD) * des;
+#pragma unroll
+            for (int t = 0; t < R; ++t) q[t * wstep] = v[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = idxD + t * Ns;
+                dst[b * dbs + (e + (e >> 4)) * des] = v[t];
+            }
+        }
+    }
+}
+
+// Per-pass twiddle tables of a power-of-two length n for the radix plan of
+// pp_fft_p2 (16 while at least 4 bits remain, then 8 / 4 / 2): for every
+// pass with Ns > 1, Ns * R entries T[t Ns + k] = exp(-2 pi i t k / (Ns R))
+// (consecutive butterflies k read consecutive entries).
+// Total length pass_twiddle_len(n) <= 2 n.
+__host__ __device__ inline int pass_twiddle_len(int n) {
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    int logNs = 0, rem = logn, len = 0;
+    while (rem > 0) {
+        const int lr = rem >= 4 ? 4 : rem;
+        if (logNs > 0) len += 1 << (logNs + lr);
+        logNs += lr;
+        rem -= lr;
+    }
+    return len;
+}
+
+// pp_fft for power-of-two n with compile-time padding of A and B; T holds
+// the pass twiddle tables of n
+template <int DIR, bool BFAST, int PADA, int PADB, typename C>
+__device__ int pp_fft_p2(C *A, int abs_, int aes, C *B, int bbs, int bes, int n, int nbatch, const C *T, int tid,
+                         int nthr) {
+    const int logn = ilog2(n), lognbatch = ilog2(nbatch);
+    int logNs = 0, rem = logn, where = 0;
+    const C *Tp = T;
+    while (rem > 0) {
+        const int lr = rem >= 4 ? 4 : rem;   // radix 16, then 8 / 4 / 2 for the rest
+        if (where == 0) {
+            if (lr == 4) pp_pass_p2<16, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+            else if (lr == 3) pp_pass_p2<8, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+            else if (lr == 2) pp_pass_p2<4, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+            else pp_pass_p2<2, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+        } else {
+            if (lr == 4) pp_pass_p2<16, DIR, BFAST, PADB, PADA>(B, bbs, bes, A, abs_, aes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+            else if (lr == 3) pp_pass_p2<8, DIR, BFAST, PADB, PADA>(B, bbs, bes, A, abs_, aes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+            else if (lr == 2) pp_pass_p2<4, DIR, BFAST, PADB, PADA>(B, bbs, bes, A, abs_, aes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+            else pp_pass_p2<2, DIR, BFAST, PADB, PADA>(B, bbs, bes, A, abs_, aes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
+        }
+        __syncthreads();
+        if (logNs > 0) Tp += 1 << (logNs + lr);
+        logNs += lr;
+        rem -= lr;
+        where ^= 1;
+    }
+    return where;
+}
+
+// Dispatch: the shift-based passes when n (and, for BFAST, nbatch) is a
+// power of two, the generic passes otherwise.  PADA / PADB must match
+// la.pad / lb.pad.
+// (W: the length-n twiddles of the generic passes; T: the pass tables of
+// the shift-based ones, used when n is a power of two)
+template <int DIR, bool BFAST, int PADA, int PADB, typename C>
+__device__ __forceinline__ int pp_fft_any(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *W, const C *T,
+                                          int tid, int nthr) {
+    if (is_pow2(n) && (!BFAST || is_pow2(nbatch)))
+        return pp_fft_p2<DIR, BFAST, PADA, PADB>(A, la.bs, la.es, B, lb.bs, lb.es, n, nbatch, T, tid, nthr);
+    return pp_fft<DIR, BFAST>(A, la, B, lb, n, nbatch, W, tid, nthr);
+}
+
 // r2c_post / c2r_pre (below) on rows in an arbitrary layout
 template <typename C>
 __device__ __forceinline__ void r2c_post_l(C *a, Lay L, int h, int batch, const C *Wp, int tid, int nthr) {
     using R = decltype(a[0].x);
-    const int npair = h / 2 + 1;
-    for (int j = tid; j < npair * batch; j += nthr) {
-        const int row = j / npair;
-        const int k = j - row * npair;
-        if (k == 0) {
-            const int i0 = L(row, 0);
-            C z0 = a[i0];
-            a[i0] = C{z0.x + z0.y, z0.x - z0.y};
-        } else {
-            const int ik = L(row, k), ih = L(row, h - k);
-            C p = a[ik], q = a[ih];
-            C ze = cscale(cadd(p, cconj(q)), R(0.5));
-            C zo = cscale(cmul_mi(csub(p, cconj(q))), R(0.5));
-            C wz = cmul(Wp[k], zo);
-            a[ik] = cadd(ze, wz);
-            if (h - k != k) a[ih] = cconj(csub(ze, wz));
+    for (int row = 0; row < batch; ++row) {
+        for (int k = tid; k <= h / 2; k += nthr) {
+            if (k == 0) {
+                const int i0 = L(row, 0);
+                C z0 = a[i0];
+                a[i0] = C{z0.x + z0.y, z0.x - z0.y};
+            } else {
+                const int ik = L(row, k), ih = L(row, h - k);
+                C p = a[ik], q = a[ih];
+                C ze = cscale(cadd(p, cconj(q)), R(0.5));
+                C zo = cscale(cmul_mi(csub(p, cconj(q))), R(0.5));
+                C wz = cmul(Wp[k], zo);
+                a[ik] = cadd(ze, wz);
+                if (h - k != k) a[ih] = cconj(csub(ze, wz));
+            }
         }
     }
 }
 
 template <typename C>
 __device__ __forceinline__ void c2r_pre_l(C *a, Lay L, int h, int batch, const C *Wp, int tid, int nthr) {
-    const int npair = h / 2 + 1;
-    for (int j = tid; j < npair * batch; j += nthr) {
-        const int row = j / npair;
-        const int k = j - row * npair;
-        if (k == 0) {
-            const int i0 = L(row, 0);
-            C x0 = a[i0];
-            a[i0] = C{x0.x + x0.y, x0.x - x0.y};
-        } else {
-            const int ik = L(row, k), ih = L(row, h - k);
-            C p = a[ik], q = a[ih];
-            C w = Wp[k];
-            C wc = cconj(w);
-            a[ik] = cadd(cadd(p, cconj(q)), cmul_i(cmul(csub(p, cconj(q)), wc)));
-            if (h - k != k) {
-                C mw = C{-w.x, -w.y};
-                a[ih] = cadd(cadd(q, cconj(p)), cmul_i(cmul(csub(q, cconj(p)), mw)));
+    for (int row = 0; row < batch; ++row) {
+        for (int k = tid; k <= h / 2; k += nthr) {
+            if (k == 0) {
+                const int i0 = L(row, 0);
+                C x0 = a[i0];
+                a[i0] = C{x0.x + x0.y, x0.x - x0.y};
+            } else {
+                const int ik = L(row, k), ih = L(row, h - k);
+                C p = a[ik], q = a[ih];
+                C w = Wp[k];
+                C wc = cconj(w);
+                a[ik] = cadd(cadd(p, cconj(q)), cmul_i(cmul(csub(p, cconj(q)), wc)));
+                if (h - k != k) {
+                    C mw = C{-w.x, -w.y};
+                    a[ih] = cadd(cadd(q, cconj(p)), cmul_i(cmul(csub(q, cconj(p)), mw)));
+                }
             }
         }
     }

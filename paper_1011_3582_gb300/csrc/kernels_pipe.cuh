@@ -22,6 +22,12 @@
 #ifndef FFTLB_NT64
 #define FFTLB_NT64 256
 #endif
+#ifndef FFTLB_MINB32
+#define FFTLB_MINB32 1
+#endif
+#ifndef FFTLB_MINB64
+#define FFTLB_MINB64 1
+#endif
 
 namespace fftlb {
 
@@ -48,9 +54,11 @@ inline size_t smem_bytes(std::initializer_list<size_t> parts) {
 template <typename real> struct KCfg;
 template <> struct KCfg<float> {
     static constexpr int NT = FFTLB_NT32;
+    static constexpr int MINB = FFTLB_MINB32;
 };
 template <> struct KCfg<double> {
     static constexpr int NT = FFTLB_NT64;
+    static constexpr int MINB = FFTLB_MINB64;
 };
 
 template <typename C>
@@ -67,11 +75,12 @@ __device__ __forceinline__ real real_at(const typename cplx_of<real>::type *buf,
 // Transforms of nrows rows of A (layout la) through a work buffer of wrows
 // padded rows, a chunk at a time; results always end in A.
 template <int DIR, typename C>
-__device__ void rows_fft_to_A(C *A, Lay la, C *wk, Lay lb, int n, int nrows, int wrows, const C *W, int nthr) {
+__device__ void rows_fft_to_A(C *A, Lay la, C *wk, Lay lb, int n, int nrows, int wrows, const C *W, const C *T,
+                              int nthr) {
     for (int r0 = 0; r0 < nrows; r0 += wrows) {
         const int nb = min(wrows, nrows - r0);
         C *a = A + (size_t)r0 * la.bs;
-        const int w = pp_fft<DIR, false>(a, la, wk, lb, n, nb, W, (int)threadIdx.x, nthr);
+        const int w = pp_fft_any<DIR, false, 0, 1>(a, la, wk, lb, n, nb, W, T, (int)threadIdx.x, nthr);
         if (w) {
             for (int i = threadIdx.x; i < nb * n; i += nthr) {
                 const int r = i / n, e = i - r * n;
@@ -99,12 +108,13 @@ __device__ __forceinline__ void k1_issue(const real *f, real *dst, uint64_t *bar
 }
 
 template <typename real, int SMAX>
-__global__ void __launch_bounds__(KCfg<real>::NT, 1) k1_pipe(const real *__restrict__ f,
+__global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) k1_pipe(const real *__restrict__ f,
                                                              typename cplx_of<real>::type *spec,
                                                              real *__restrict__ fields,
                                                              const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                              const typename cplx_of<real>::type *__restrict__ Wp_g,
-                                                             KP<real> P, int CH, int *err) {
+                                                             const typename cplx_of<real>::type *__restrict__ Tr_g,
+                                                             int ntr, KP<real> P, int CH, int *err) {
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -115,6 +125,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k1_pipe(const real *__restr
     SmemCursor sc{smem_raw, 0u};
     C *Wr = (C *)sc.take(h * sizeof(C));
     C *Wp = (C *)sc.take(h * sizeof(C));
+    C *Tr = (C *)sc.take(ntr * sizeof(C));
     real *buf0 = (real *)sc.take((size_t)CH * nx * sizeof(real));
     real *buf1 = (real *)sc.take((size_t)CH * nx * sizeof(real));
     C *wk = (C *)sc.take((size_t)CH * ph * sizeof(C));
@@ -129,6 +140,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k1_pipe(const real *__restr
     }
     load_tab(Wr, Wr_g, h, NT);
     load_tab(Wp, Wp_g, h, NT);
+    load_tab(Tr, Tr_g, ntr, NT);
     __syncthreads();
     if (tid == 0) {
         if (njobs > 0) k1_issue(f, buf0, &bar0, 0, nchunk, CH, nx, N);
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k1_pipe(const real *__restr
         __syncthreads();
         const int r0 = (i0 == 0) ? 1 : 0;   // the rest velocity is not transformed
         if (nf > r0) {
-            const int w = pp_fft<-1, false>(Bc + (size_t)r0 * h, la, wk, lb, h, nf - r0, Wr, tid, NT);
+            const int w = pp_fft_any<-1, false, 0, 1>(Bc + (size_t)r0 * h, la, wk, lb, h, nf - r0, Wr, Tr, tid, NT);
             C *res = w ? wk : Bc + (size_t)r0 * h;
             const Lay lr = w ? lb : la;
             r2c_post_l(res, lr, h, nf - r0, Wp, tid, NT);
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k1_pipe(const real *__restr
                 a0[s] = a1[s] = a2[s] = a3[s] = real(0);
             }
             __syncthreads();
-            const int w = pp_fft<-1, false>(Bc, la, wk, lb, h, 6, Wr, tid, NT);
+            const int w = pp_fft_any<-1, false, 0, 1>(Bc, la, wk, lb, h, 6, Wr, Tr, tid, NT);
             C *res = w ? wk : Bc;
             const Lay lr = w ? lb : la;
             r2c_post_l(res, lr, h, 6, Wp, tid, NT);
@@ -254,8 +266,8 @@ template <typename real>
 __device__ __forceinline__ void col_multiply(typename cplx_of<real>::type *out, Lay lo,
                                              const typename cplx_of<real>::type *X0, Lay l0,
                                              const typename cplx_of<real>::type *X1, Lay l1, const GroupDesc &g,
-                                             int o, const real *kxt, const real *kyt, int kx0, int TW, int ny, int h,
-                                             real scale, int nthr) {
+                                             int o, const real *kxt, const real *kyt, int kx0, int TW, int lgTW,
+                                             int ny, int h, real scale, int nthr) {
     using C = typename cplx_of<real>::type;
     const bool two = g.nterm[o] > 1;
     const C *t0 = g.term_in[o][0] ? X1 : X0;
@@ -268,7 +280,7 @@ __device__ __forceinline__ void col_multiply(typename cplx_of<real>::type *out, 
                q4 = (real)g.c[o][1][4];
     const int tile = TW * ny;
     for (int idx = threadIdx.x; idx < tile; idx += nthr) {
-        const int e = idx / TW, c = idx - e * TW;
+        const int e = idx >> lgTW, c = idx & (TW - 1);
         const int kx = kx0 + c;
         if (kx == 0) continue;
         const real ax = kxt[kx], ay = kyt[e];
@@ -325,12 +337,13 @@ __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDes
 // MULTI = false: every group has one input and one output in place
 // (convection); MULTI = true: up to 2 inputs and several outputs.
 template <typename real, bool MULTI>
-__global__ void __launch_bounds__(KCfg<real>::NT, 1) kcol_pipe(typename cplx_of<real>::type *spec,
+__global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) kcol_pipe(typename cplx_of<real>::type *spec,
                                                                const GroupDesc *__restrict__ groups, int ngroups,
                                                                const real *__restrict__ kxt,
                                                                const real *__restrict__ kyt,
                                                                const typename cplx_of<real>::type *__restrict__ Wc_g,
-                                                               KP<real> P, int TW, int BOXR,
+                                                               const typename cplx_of<real>::type *__restrict__ Tc_g,
+                                                               int ntc, KP<real> P, int TW, int BOXR,
                                                                const __grid_constant__ CUtensorMap tmap, int *err) {
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real>::NT;
@@ -342,8 +355,12 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) kcol_pipe(typename cplx_of<
     const size_t slot = (size_t)ny * h;
     const int tile = TW * ny;
     const int ptile = TW * padded_len(ny);
+    const int lgTW = ilog2(TW);   // TW is a power of two
     SmemCursor sc{smem_raw, 0u};
     C *Wc = (C *)sc.take(ny * sizeof(C));
+    C *Tc = (C *)sc.take(ntc * sizeof(C));
+    real *kxs = (real *)sc.take((size_t)(h + 1 + ny) * sizeof(real));   // k_x then k_y tables
+    real *kys = kxs + h + 1;
     C *buf0 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
     C *buf1 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
     C *wk0 = (C *)sc.take((size_t)ptile * sizeof(C));
@@ -358,6 +375,9 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) kcol_pipe(typename cplx_of<
         mbar_init_fence();
     }
     load_tab(Wc, Wc_g, ny, NT);
+    load_tab(Tc, Tc_g, ntc, NT);
+    load_tab(kxs, kxt, h + 1, NT);
+    load_tab(kys, kyt, ny, NT);
     __syncthreads();
     if (tid == 0) {
         if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, TW, ny, BOXR, &tmap);
@@ -389,46 +409,51 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) kcol_pipe(typename cplx_of<
         C *gout;
         if (!MULTI) {
             // convection: forward, multiply in place, inverse, store
-            const int w1 = pp_fft<-1, true>(in0, lt, wk0, lw, ny, TW, Wc, tid, NT);
+            const int w1 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
             C *X = w1 ? wk0 : in0;
             C *Y = w1 ? in0 : wk0;
             const Lay lx = w1 ? lw : lt, ly = w1 ? lt : lw;
-            col_multiply<real>(X, lx, X, lx, X, lx, gd, 0, kxt, kyt, kx0, TW, ny, h, scale, NT);
+            col_multiply<real>(X, lx, X, lx, X, lx, gd, 0, kxs, kys, kx0, TW, lgTW, ny, h, scale, NT);
             __syncthreads();
-            const int w2 = pp_fft<+1, true>(X, lx, Y, ly, ny, TW, Wc, tid, NT);
+            const int w2 = w1 ? pp_fft_any<+1, true, 1, 0>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT)
+                              : pp_fft_any<+1, true, 0, 1>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT);
             const C *R = w2 ? Y : X;
             const Lay lr = w2 ? ly : lx;
             gout = spec + (size_t)gd.out_slot[0] * slot + kx0;
             for (int idx = tid; idx < tile; idx += NT) {
-                const int e = idx / TW, c = idx - e * TW;
+                const int e = idx >> lgTW, c = idx & (TW - 1);
                 gout[(size_t)e * h + c] = R[lr(c, e)];
             }
         } else {
             // X0 in {in0, wk0}, X1 in {in1, wk1}; outputs ping-pong between
             // the two buffers left free
             C *in1 = in0 + tile;
-            const int w0 = pp_fft<-1, true>(in0, lt, wk0, lw, ny, TW, Wc, tid, NT);
+            const int w0 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
             C *X0 = w0 ? wk0 : in0;
             C *F0 = w0 ? in0 : wk0;
             const Lay lx0 = w0 ? lw : lt, lf0 = w0 ? lt : lw;
             C *X1 = in1, *F1 = wk1;
             Lay lx1 = lt, lf1 = lw;
             if (gd.nin > 1) {
-                const int w1 = pp_fft<-1, true>(in1, lt, wk1, lw, ny, TW, Wc, tid, NT);
+                const int w1 = pp_fft_any<-1, true, 0, 1>(in1, lt, wk1, lw, ny, TW, Wc, Tc, tid, NT);
                 X1 = w1 ? wk1 : in1;
                 F1 = w1 ? in1 : wk1;
                 lx1 = w1 ? lw : lt;
                 lf1 = w1 ? lt : lw;
             }
             for (int o = 0; o < gd.nout; ++o) {
-                col_multiply<real>(F0, lf0, X0, lx0, X1, lx1, gd, o, kxt, kyt, kx0, TW, ny, h, scale, NT);
+                col_multiply<real>(F0, lf0, X0, lx0, X1, lx1, gd, o, kxs, kys, kx0, TW, lgTW, ny, h, scale, NT);
                 __syncthreads();
-                const int w2 = pp_fft<+1, true>(F0, lf0, F1, lf1, ny, TW, Wc, tid, NT);
+                int w2;
+                if (lf0.pad) w2 = lf1.pad ? pp_fft_any<+1, true, 1, 1>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT)
+                                          : pp_fft_any<+1, true, 1, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT);
+                else w2 = lf1.pad ? pp_fft_any<+1, true, 0, 1>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT)
+                                  : pp_fft_any<+1, true, 0, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT);
                 const C *R = w2 ? F1 : F0;
                 const Lay lr = w2 ? lf1 : lf0;
                 gout = spec + (size_t)gd.out_slot[o] * slot + kx0;
                 for (int idx = tid; idx < tile; idx += NT) {
-                    const int e = idx / TW, c = idx - e * TW;
+                    const int e = idx >> lgTW, c = idx & (TW - 1);
                     gout[(size_t)e * h + c] = R[lr(c, e)];
                 }
                 __syncthreads();
@@ -454,8 +479,9 @@ template <typename real>
 __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spec, const real *__restrict__ fields,
                                                real *__restrict__ aux,
                                                const typename cplx_of<real>::type *__restrict__ Wr_g,
-                                               const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P,
-                                               int WR, int *err) {
+                                               const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                               const typename cplx_of<real>::type *__restrict__ Tr_g, int ntr,
+                                               KP<real> P, int WR, int *err) {
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -465,6 +491,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     SmemCursor sc{smem_raw, 0u};
     C *Wr = (C *)sc.take(h * sizeof(C));
     C *Wp = (C *)sc.take(h * sizeof(C));
+    C *Tr = (C *)sc.take(ntr * sizeof(C));
     C *d = (C *)sc.take((size_t)ND1 * h * sizeof(C));
     C *wk = (C *)sc.take((size_t)WR * ph * sizeof(C));
     real *rT = (real *)sc.take((size_t)2 * nx * sizeof(real));
@@ -481,13 +508,14 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     }
     load_tab(Wr, Wr_g, h, NT3);
     load_tab(Wp, Wp_g, h, NT3);
+    load_tab(Tr, Tr_g, ntr, NT3);
     if (!block_wait(&bar, 0, err)) {
         mbar_wait_bounded(&bar, 0);
         return;
     }
     c2r_pre_l(d, la, h, ND1, Wp, tid, NT3);
     __syncthreads();
-    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, NT3);
+    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, Tr, NT3);
     const C *res = d;
     const Lay lr = la;
     real *dw = reinterpret_cast<real *>(d);
@@ -524,7 +552,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
         dw[4 * nx + x] = q2 * Ty;
     }
     __syncthreads();
-    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, NT3);
+    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, Tr, NT3);
     C *res2 = d;
     const Lay lr2 = la;
     r2c_post_l(res2, lr2, h, 5, Wp, tid, NT3);
@@ -573,13 +601,14 @@ __device__ __forceinline__ void k5_issue_head(const typename cplx_of<real>::type
 // NHB head buffers (1 or 2): the head of row ri lives in buffer ri % NHB and
 // is prefetched NHB rows ahead.
 template <typename real, int SMAX>
-__global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx_of<real>::type *spec,
+__global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) k5_pipe(const typename cplx_of<real>::type *spec,
                                                              const real *__restrict__ fields,
                                                              const real *__restrict__ aux, const real *fcur,
                                                              const real *fbase, real *fout, real alpha, real beta,
                                                              const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                              const typename cplx_of<real>::type *__restrict__ Wp_g,
-                                                             KP<real> P, int CH, int NHB, int *err) {
+                                                             const typename cplx_of<real>::type *__restrict__ Tr_g,
+                                                             int ntr, KP<real> P, int CH, int NHB, int *err) {
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -590,6 +619,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx
     SmemCursor sc{smem_raw, 0u};
     C *Wr = (C *)sc.take(h * sizeof(C));
     C *Wp = (C *)sc.take(h * sizeof(C));
+    C *Tr = (C *)sc.take(ntr * sizeof(C));
     real *head0 = (real *)sc.take((size_t)NHEAD * nx * sizeof(real));
     real *head1 = NHB > 1 ? (real *)sc.take((size_t)NHEAD * nx * sizeof(real)) : head0;
     real *buf0 = (real *)sc.take((size_t)CH * nx * sizeof(real));
@@ -608,6 +638,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx
     }
     load_tab(Wr, Wr_g, h, NT);
     load_tab(Wp, Wp_g, h, NT);
+    load_tab(Tr, Tr_g, ntr, NT);
     __syncthreads();
     if (tid == 0) {
         if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, N, slot, h);
@@ -644,7 +675,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx
             C *l2 = reinterpret_cast<C *>(H);
             c2r_pre_l(l2, la, h, 3, Wp, tid, NT);
             __syncthreads();
-            const int w = pp_fft<+1, false>(l2, la, wk, lb, h, 3, Wr, tid, NT);
+            const int w = pp_fft_any<+1, false, 0, 1>(l2, la, wk, lb, h, 3, Wr, Tr, tid, NT);
             const C *lres = w ? wk : l2;
             const Lay llr = w ? lb : la;
             // per-site coefficients, written over the head rows (same site,
@@ -701,7 +732,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx
         C *Bc = reinterpret_cast<C *>(B);
         c2r_pre_l(Bc, la, h, nv, Wp, tid, NT);
         __syncthreads();
-        const int w = pp_fft<+1, false>(Bc, la, wk, lb, h, nv, Wr, tid, NT);
+        const int w = pp_fft_any<+1, false, 0, 1>(Bc, la, wk, lb, h, nv, Wr, Tr, tid, NT);
         const C *cres = w ? wk : Bc;
         const Lay lcr = w ? lb : la;
 #pragma unroll 1
@@ -709,14 +740,17 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx
             const int x = tid + s * NT;
             if (x >= nx) continue;
             real fc[CHMAX5], fb[CHMAX5];
+            const size_t o0 = (size_t)(1 + v0) * N + (size_t)y * nx + x;
+            const real *pc = fcur + o0;
+            const real *pb = fbase + o0;
 #pragma unroll
             for (int r = 0; r < CHMAX5; ++r) {
                 if (r < nv) {
-                    const size_t o = (size_t)(1 + v0 + r) * N + (size_t)y * nx + x;
-                    fc[r] = fcur[o];
-                    fb[r] = with_base ? fbase[o] : real(0);
+                    fc[r] = pc[r * N];
+                    fb[r] = with_base ? pb[r * N] : real(0);
                 }
             }
+            real *po = fout + o0;
             const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
             const real e0 = H[x], e1x = H[nx + x], e1y = H[2 * nx + x], CC = H[7 * nx + x];
             real F[5];
@@ -742,7 +776,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, 1) k5_pipe(const typename cplx
                     const real rhs = -conv - (fc[r] - fe) * itau + I;                       // Eq. 10
                     real fn = beta * (fc[r] + dt * rhs);
                     if (with_base) fn += alpha * fb[r];
-                    fout[(size_t)i * N + (size_t)y * nx + x] = fn;
+                    po[r * N] = fn;
                 }
             }
         }
