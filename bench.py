@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 companion measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the batched sweep (64 runs of uneven grids replayed as one CUDA graph)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -304,6 +306,38 @@ def main():
         e2e = {"value": world * n * n * K / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": fb / K,
                "d2h_bytes_per_step": 48 + fb / K}
 
+    sweep = None
+    if args.sweep:
+        # batched phase-diagram sweep: 64 spinodal quenches (rho_c, T_r T_c) of
+        # uneven grids, one CUDA graph per step
+        plan = workloads.sweep_plan(64, seed=3)
+        plist, flist = [], []
+        for r_, (n_, tr) in enumerate(plan):
+            flist.append(workloads.spinodal(n_, n_, RHOC, tr * TC, amp=0.01, seed=100 + r_))
+            plist.append(fftlb.params(nx=n_, ny=n_, a=A, b=B, precision=args.precision, integrator=3, window=4))
+        t0 = time.perf_counter()
+        bt = fftlb.Batch(plist, autotune=True, stream=stream.cuda_stream)
+        t_create = time.perf_counter() - t0
+        for r, fl_ in enumerate(flist):
+            bt.set_fields(r, *fl_)
+        bt.step(3)
+        torch.cuda.synchronize()
+        ks = max(5, K // 2)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        bt.step(ks)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sms = maxed(ev0.elapsed_time(ev1))
+        sites = sum(n_ * n_ for n_, _ in plan)
+        sweep = {"value": world * sites * ks / (sms * 1e-3) / 1e6, "unit": "MLUPS", "runs": len(plan),
+                 "grids": {str(g): sum(1 for n_, _ in plan if n_ == g) for g in (128, 256, 384, 512)},
+                 "steps": ks, "ms_per_step": sms / ks, "gpu_launches_per_step": bt.launches_per_step(),
+                 "graph_launches_per_step": 1, "create_and_autotune_s": t_create}
+        bt.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
@@ -321,7 +355,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "kernels": kernels, "alg_bytes_per_step": step_bytes,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
-                "fp64": fp64, "invariants_after": inv}
+                "fp64": fp64, "sweep": sweep, "invariants_after": inv}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -151,6 +151,47 @@ fftlb_status fftlb_profile(fftlb_t h, int enable);
 fftlb_status fftlb_profile_read(fftlb_t h, double *ms, long *launches, double *bytes, int nkinds);
 const char *fftlb_kernel_name(int kind);
 
+/* Launch-parameter tuning of the pipelined stage kernels.  The runtime
+ * parameters are tuning[5] = {column tile width of the convection pass,
+ * column tile width of the level-1/2 passes, distribution rows per chunk of
+ * the forward row kernel, convection rows per chunk of the final row kernel,
+ * head buffers of the final row kernel (1 or 2)}.  fftlb_tuning reads them
+ * (set = 0) or applies them (set = 1; 0 entries keep the current value;
+ * FFTLB_ERR_ARG if a value is invalid or does not fit in shared memory).
+ * fftlb_autotune times candidate values on the handle's current state
+ * (saved and restored, so the state is unchanged) one parameter at a time,
+ * keeps the fastest, and returns the best stage time in *stage_ms (may be
+ * NULL).  Neither changes results: only the order of independent work. */
+fftlb_status fftlb_autotune(fftlb_t h, double *stage_ms);
+fftlb_status fftlb_tuning(fftlb_t h, int tuning[5], int set);
+
+/* Batched sweep: nruns independent problems (each its own grid, parameters
+ * and state; the same velocity set) advanced together.  One time step of
+ * every run, the runs one after another on one internal stream, is
+ * captured once into a CUDA graph; fftlb_batch_step(b, n) replays it n
+ * times on cuda_stream (borrowed; NULL = legacy default stream).  With
+ * autotune != 0, fftlb_batch_create tunes one run of every distinct
+ * (nx, ny, precision, integrator) and applies its parameters to all runs of
+ * that shape.  check_every is ignored (no host checks inside replays); call
+ * fftlb_batch_invariants to inspect a run.  Per-run calls take the run
+ * index; they are ordered after the steps already launched.  Results of a
+ * run are identical to those of a single handle with the same parameters.
+ * Memory: as nruns single handles. */
+typedef struct fftlb_batch_s *fftlb_batch_t;
+fftlb_status fftlb_batch_create(fftlb_batch_t *b, int nruns, const fftlb_params *params,
+                                const fftlb_velset *velset, int autotune, void *cuda_stream);
+fftlb_status fftlb_batch_set_fields(fftlb_batch_t b, int run, const double *rho, const double *ux,
+                                    const double *uy, const double *T, int on_device);
+fftlb_status fftlb_batch_step(fftlb_batch_t b, long nsteps);
+fftlb_status fftlb_batch_fields(fftlb_batch_t b, int run, double *rho, double *ux, double *uy,
+                                double *T, int on_device);
+fftlb_status fftlb_batch_get_f(fftlb_batch_t b, int run, double *f, int on_device);
+fftlb_status fftlb_batch_invariants(fftlb_batch_t b, int run, double out[6]);
+fftlb_status fftlb_batch_tuning(fftlb_batch_t b, int run, int tuning[5]);
+long fftlb_batch_launches_per_step(fftlb_batch_t b);
+fftlb_status fftlb_batch_destroy(fftlb_batch_t b);
+const char *fftlb_batch_last_error(fftlb_batch_t b);
+
 /* Windowed spectral gradient of one fp64 device field g[ny][nx] into
  * out[2][ny][nx] (out[0] = D_x g, out[1] = D_y g), like fftlb_gradient with
  * nfields = 1, but without a handle and without allocating device memory.

@@ -182,6 +182,22 @@ fftlb_status fftlb_profile_read(fftlb_t h, double *ms, long *launches, double *b
     return st.good() ? FFTLB_OK : fail(h, st);
 }
 
+fftlb_status fftlb_autotune(fftlb_t h, double *stage_ms) {
+    if (!h) return fail(nullptr, FFTLB_ERR_ARG, "NULL handle");
+    fftlb::Status st = h->eng->autotune(stage_ms);
+    return st.good() ? FFTLB_OK : fail(h, st);
+}
+
+fftlb_status fftlb_tuning(fftlb_t h, int tuning[5], int set) {
+    if (!h || !tuning) return fail(h, FFTLB_ERR_ARG, "NULL handle or tuning");
+    if (!set) {
+        h->eng->get_tuning(tuning);
+        return FFTLB_OK;
+    }
+    fftlb::Status st = h->eng->set_tuning(tuning);
+    return st.good() ? FFTLB_OK : fail(h, st);
+}
+
 const char *fftlb_kernel_name(int kind) {
     return (kind >= 0 && kind < fftlb::KK_COUNT) ? fftlb::kKernelNames[kind] : "";
 }

@@ -10,10 +10,11 @@
 
 namespace fftlb {
 
-// polls of mbarrier.try_wait before a stage is declared stuck (each poll
-// may suspend the thread for a hardware-defined interval; together they
-// bound a wait to well under a minute)
-constexpr int kWaitPolls = 1 << 22;
+// A stage whose copies have not landed after this many nanoseconds of
+// polling (read from the %globaltimer nanosecond clock) is declared stuck;
+// kWaitPolls caps the polls as well, in case that clock does not advance.
+constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned kWaitPolls = 1u << 28;
 
 // bits of the device error word
 constexpr int kErrWaitTimeout = 1;
@@ -53,10 +54,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // bounded wait by this thread; false if the phase did not complete
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (int i = 0; i < kWaitPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned i = 1; i < kWaitPolls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 

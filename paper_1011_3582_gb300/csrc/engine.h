@@ -42,6 +42,18 @@ class Engine {
     // kernel timing: CUDA events around every stage launch, by kernel kind
     virtual Status profile(int enable) = 0;
     virtual Status profile_read(double *ms, long *launches, double *bytes, int nkinds) = 0;
+    // one time step enqueued on the handle's stream with no host
+    // synchronisation (no state checks): capturable in a CUDA graph
+    virtual Status enqueue_step() = 0;
+    virtual cudaStream_t stream() const = 0;
+    // launch-parameter tuning: the runtime parameters of the pipelined
+    // kernels (column tile widths, row-chunk sizes, head buffering)
+    static constexpr int NTUNE = 5;
+    virtual void get_tuning(int t[NTUNE]) const = 0;
+    virtual Status set_tuning(const int t[NTUNE]) = 0;
+    // times candidate parameters on the current state (saved and restored)
+    // and keeps the fastest; *stage_ms receives the best stage time
+    virtual Status autotune(double *stage_ms) = 0;
 };
 
 // kernel kinds of one stage (index into the profile arrays)

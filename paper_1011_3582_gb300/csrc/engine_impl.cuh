@@ -1358,13 +1358,19 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
+    // (the shared-memory opt-in is a per-function, process-wide attribute:
+    // always the full budget, so that handles of different grids never
+    // lower it below one another's needs)
     template <typename K> Status occupancy(K kernel, int nthreads, size_t smem, int *blocks) {
-        FFTLB_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FFTLB_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
         FFTLB_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, nthreads, smem));
         return Status::ok();
     }
 
+    size_t budget_ = 0;
+
     Status configure_pipe(size_t budget) {
+        budget_ = budget;
         const size_t cs = sizeof(C), rs = sizeof(real);
         constexpr int NT = KCfg<real>::NT;
         if (((size_t)nx_ * rs) % 16 != 0)
@@ -1498,6 +1504,137 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
+  public:
+    Status enqueue_step() override {
+        Status st;
+        if (p_.integrator == 1) return stage(f0_, nullptr, f0_, real(0), real(1));
+        if (!(st = stage(f0_, nullptr, f1_, real(0), real(1))).good()) return st;
+        if (!(st = stage(f1_, f0_, f1_, real(0.75), real(0.25))).good()) return st;
+        return stage(f1_, f0_, f0_, real(1.0 / 3.0), real(2.0 / 3.0));
+    }
+
+    cudaStream_t stream() const override { return stream_; }
+
+    void get_tuning(int t[NTUNE]) const override {
+        t[0] = TWc_;
+        t[1] = TWl_;
+        t[2] = CH1_;
+        t[3] = CH5_;
+        t[4] = NHB5_;
+    }
+
+    // apply explicit parameters (0 = keep): recompute shared-memory sizes,
+    // grids and tensor maps; rejects values that do not fit
+    Status set_tuning(const int t[NTUNE]) override {
+        const size_t cs = sizeof(C), rs = sizeof(real);
+        constexpr int NT = KCfg<real>::NT;
+        const size_t ph = (size_t)padded_len(h_), pny = (size_t)padded_len(ny_);
+        const int twc = t[0] ? t[0] : TWc_, twl = t[1] ? t[1] : TWl_, ch1 = t[2] ? t[2] : CH1_;
+        const int ch5 = t[3] ? t[3] : CH5_, nhb = t[4] ? t[4] : NHB5_;
+        auto twok = [&](int tw) { return tw >= 1 && tw <= 8 && (tw & (tw - 1)) == 0 && h_ % tw == 0 && (2 * tw * rs) % 16 == 0; };
+        if (!twok(twc) || !twok(twl) || ch1 < 6 || ch1 > 8 || ch5 < 2 || ch5 > CHMAX5 || (ch5 & 1) || nhb < 1 || nhb > 2)
+            return Status::err(FFTLB_ERR_ARG, "tuning parameters out of range");
+        const size_t sm1 = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ch1 * nx_ * rs, (size_t)ch1 * nx_ * rs, ch1 * ph * cs});
+        const size_t kt = (h_ + 1 + ny_) * rs;
+        const size_t tc = (size_t)twc * ny_ * cs, ptc = (size_t)twc * pny * cs;
+        const size_t tl = (size_t)twl * ny_ * cs, ptl = (size_t)twl * pny * cs;
+        const size_t smc = smem_bytes({ny_ * cs, ntc_ * cs, kt, tc, tc, ptc});
+        const size_t sml = smem_bytes({ny_ * cs, ntc_ * cs, kt, 2 * tl, 2 * tl, ptl, ptl});
+        const size_t head = (size_t)NHEAD * nx_ * rs;
+        const size_t sm5 = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, head, nhb > 1 ? head : 0, (size_t)ch5 * nx_ * rs,
+                                       (size_t)ch5 * nx_ * rs, (size_t)std::max(ch5, 3) * ph * cs});
+        if (sm1 > budget_ || smc > budget_ || sml > budget_ || sm5 > budget_)
+            return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
+        Status st;
+        int nb = 0;
+        if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, sm1, &nb);
+        else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, sm1, &nb);
+        else st = occupancy(k1_pipe<real, 4>, NT, sm1, &nb);
+        if (!st.good()) return st;
+        const int g1 = std::min(ny_, std::max(1, nb) * nsm_);
+        if (!(st = occupancy(kcol_pipe<real, false>, NT, smc, &nb)).good()) return st;
+        const int gc = std::max(1, nb) * nsm_;
+        if (!(st = occupancy(kcol_pipe<real, true>, NT, sml, &nb)).good()) return st;
+        const int gl = std::max(1, nb) * nsm_;
+        if (SMAX5_ == 1) st = occupancy(k5_pipe<real, 1>, NT, sm5, &nb);
+        else if (SMAX5_ == 2) st = occupancy(k5_pipe<real, 2>, NT, sm5, &nb);
+        else st = occupancy(k5_pipe<real, 4>, NT, sm5, &nb);
+        if (!st.good()) return st;
+        const int g5 = std::min(ny_, std::max(1, nb) * nsm_);
+        CUtensorMap mc, ml;
+        if (!(st = make_tmap(&mc, twc)).good()) return st;
+        if (!(st = make_tmap(&ml, twl)).good()) return st;
+        TWc_ = twc;
+        TWl_ = twl;
+        CH1_ = ch1;
+        CH5_ = ch5;
+        NHB5_ = nhb;
+        smem1_ = sm1;
+        smemc_ = smc;
+        smeml_ = sml;
+        smem5_ = sm5;
+        grid1_ = g1;
+        gridc_ = gc;
+        gridl_ = gl;
+        grid5_ = g5;
+        tmap_conv_ = mc;
+        tmap_l1_ = ml;
+        return Status::ok();
+    }
+
+    Status autotune(double *stage_ms) override {
+        // save f^n; candidates run stages on the current state
+        double *save = reinterpret_cast<double *>(scratch_d_);   // >= 33 N doubles = 33 N reals of either width
+        FFTLB_CU(cudaMemcpyAsync(save, f0_, Q * N_ * sizeof(real), cudaMemcpyDeviceToDevice, stream_));
+        cudaEvent_t e0, e1;
+        FFTLB_CU(cudaEventCreate(&e0));
+        FFTLB_CU(cudaEventCreate(&e1));
+        auto time_stage = [&](double *ms) -> Status {
+            Status st;
+            for (int w = 0; w < 2; ++w)
+                if (!(st = stage(f0_, nullptr, f1_ ? f1_ : f0_, real(0), real(1))).good()) return st;
+            FFTLB_CU(cudaEventRecord(e0, stream_));
+            for (int w = 0; w < 3; ++w)
+                if (!(st = stage(f0_, nullptr, f1_ ? f1_ : f0_, real(0), real(1))).good()) return st;
+            FFTLB_CU(cudaEventRecord(e1, stream_));
+            FFTLB_CU(cudaEventSynchronize(e1));
+            float t = 0;
+            FFTLB_CU(cudaEventElapsedTime(&t, e0, e1));
+            *ms = t / 3.0;
+            return Status::ok();
+        };
+        int best[NTUNE];
+        get_tuning(best);
+        double best_ms = 0;
+        Status st = time_stage(&best_ms);
+        const int cand[NTUNE][4] = {{8, 4, 2, 1}, {8, 4, 2, 1}, {8, 7, 6, 0}, {8, 6, 4, 2}, {2, 1, 0, 0}};
+        for (int p = 0; p < NTUNE && st.good(); ++p) {
+            for (int c = 0; c < 4 && cand[p][c]; ++c) {
+                int t[NTUNE];
+                for (int q = 0; q < NTUNE; ++q) t[q] = best[q];
+                if (cand[p][c] == best[p]) continue;
+                t[p] = cand[p][c];
+                if (!set_tuning(t).good()) continue;   // does not fit: skip
+                double ms = 0;
+                if (!(st = time_stage(&ms)).good()) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best[p] = t[p];
+                }
+            }
+            Status s2 = set_tuning(best);
+            if (st.good() && !s2.good()) st = s2;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (!st.good()) return st;
+        FFTLB_CU(cudaMemcpyAsync(f0_, save, Q * N_ * sizeof(real), cudaMemcpyDeviceToDevice, stream_));
+        FFTLB_CU(cudaStreamSynchronize(stream_));
+        if (stage_ms) *stage_ms = best_ms;
+        return Status::ok();
+    }
+
+  private:
     Status launch_col(int first, int count, bool level1) {
         if (level1)
             kcol_pipe<real, true><<<gridl_, KCfg<real>::NT, smeml_, stream_>>>(spec_, groups_ + first, count, kxt_,

@@ -500,6 +500,9 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_init_fence();
+    }
+    __syncthreads();   // the barrier is initialised before any thread polls it
+    if (tid == 0) {
         mbar_expect_tx(&bar, (uint32_t)(ND1 + 2) * rowbytes);
         for (int o = 0; o < ND1; ++o)
             bulk_g2s(d + (size_t)o * h, spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h, rowbytes, &bar);

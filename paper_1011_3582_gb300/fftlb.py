@@ -27,7 +27,10 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_CUDA", "ERR_UNSTABLE", "ERR_TIM
 EXPORTED = ["fftlb_create", "fftlb_set_fields", "fftlb_step", "fftlb_fields", "fftlb_get_f",
             "fftlb_set_f", "fftlb_invariants", "fftlb_gradient", "fftlb_save", "fftlb_load",
             "fftlb_destroy", "fftlb_last_error", "fftlb_launches_per_step", "fftlb_profile",
-            "fftlb_profile_read", "fftlb_kernel_name", "fftlb_gradient_static"]
+            "fftlb_profile_read", "fftlb_kernel_name", "fftlb_gradient_static", "fftlb_autotune",
+            "fftlb_tuning", "fftlb_batch_create", "fftlb_batch_set_fields", "fftlb_batch_step",
+            "fftlb_batch_fields", "fftlb_batch_get_f", "fftlb_batch_invariants", "fftlb_batch_tuning",
+            "fftlb_batch_launches_per_step", "fftlb_batch_destroy", "fftlb_batch_last_error"]
 
 
 class fftlb_params(ct.Structure):
@@ -64,10 +67,26 @@ _lib.fftlb_profile.argtypes = [_h, ct.c_int]
 _lib.fftlb_profile_read.argtypes = [_h, ct.POINTER(ct.c_double), ct.POINTER(ct.c_long),
                                     ct.POINTER(ct.c_double), ct.c_int]
 _lib.fftlb_gradient_static.argtypes = [_p, _p, ct.c_int, ct.c_int, ct.c_double, ct.c_int, _p]
+_lib.fftlb_autotune.argtypes = [_h, ct.POINTER(ct.c_double)]
+_lib.fftlb_tuning.argtypes = [_h, ct.POINTER(ct.c_int), ct.c_int]
+_lib.fftlb_batch_create.argtypes = [ct.POINTER(_h), ct.c_int, ct.POINTER(fftlb_params), ct.POINTER(fftlb_velset),
+                                    ct.c_int, _p]
+_lib.fftlb_batch_set_fields.argtypes = [_h, ct.c_int, _p, _p, _p, _p, ct.c_int]
+_lib.fftlb_batch_step.argtypes = [_h, ct.c_long]
+_lib.fftlb_batch_fields.argtypes = [_h, ct.c_int, _p, _p, _p, _p, ct.c_int]
+_lib.fftlb_batch_get_f.argtypes = [_h, ct.c_int, _p, ct.c_int]
+_lib.fftlb_batch_invariants.argtypes = [_h, ct.c_int, ct.POINTER(ct.c_double)]
+_lib.fftlb_batch_tuning.argtypes = [_h, ct.c_int, ct.POINTER(ct.c_int)]
+_lib.fftlb_batch_launches_per_step.argtypes = [_h]
+_lib.fftlb_batch_launches_per_step.restype = ct.c_long
+_lib.fftlb_batch_destroy.argtypes = [_h]
+_lib.fftlb_batch_last_error.argtypes = [_h]
+_lib.fftlb_batch_last_error.restype = ct.c_char_p
 _lib.fftlb_kernel_name.argtypes = [ct.c_int]
 _lib.fftlb_kernel_name.restype = ct.c_char_p
 for _n in EXPORTED:
-    if _n not in ("fftlb_last_error", "fftlb_launches_per_step", "fftlb_kernel_name"):
+    if _n not in ("fftlb_last_error", "fftlb_launches_per_step", "fftlb_kernel_name",
+                  "fftlb_batch_launches_per_step", "fftlb_batch_last_error"):
         getattr(_lib, _n).restype = ct.c_int
 
 
@@ -77,14 +96,31 @@ class FFTLBError(RuntimeError):
         self.status = status
 
 
-def _addr(x, on_device):
+def _addr(x, on_device, count=None):
+    """Address of a buffer handed to the C calls.  Host buffers: C-contiguous
+    float64 numpy arrays; device buffers: torch tensors (float64, contiguous,
+    on a CUDA device) or raw integer addresses.  count: required number of
+    float64 elements (checked for arrays and tensors)."""
     if x is None:
         return None
     if on_device:
-        return int(x) if isinstance(x, int) else int(x.data_ptr())
+        if isinstance(x, int):
+            return x
+        if not (x.is_cuda and x.dtype == torch_float64() and x.is_contiguous()):
+            raise TypeError("device buffers must be contiguous float64 CUDA tensors")
+        if count is not None and x.numel() != count:
+            raise ValueError(f"device buffer has {x.numel()} elements, expected {count}")
+        return int(x.data_ptr())
     if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
         raise TypeError("host buffers must be C-contiguous float64 numpy arrays")
+    if count is not None and x.size != count:
+        raise ValueError(f"host buffer has {x.size} elements, expected {count}")
     return x.ctypes.data
+
+
+def torch_float64():
+    import torch
+    return torch.float64
 
 
 def params(nx, ny, dx=1.0 / 256, dt=1e-5, tau=1e-2, a=9.0 / 8.0, b=1.0 / 3.0, K=1e-5, H=0.0,
@@ -117,8 +153,12 @@ class Handle:
     def shape(self):
         return (self.params.ny, self.params.nx)
 
+    @property
+    def sites(self):
+        return self.params.nx * self.params.ny
+
     def set_fields(self, rho, ux, uy, T, on_device=False):
-        a = [_addr(v, on_device) for v in (rho, ux, uy, T)]
+        a = [_addr(v, on_device, self.sites) for v in (rho, ux, uy, T)]
         self._check(_lib.fftlb_set_fields(self._h, *a, int(on_device)))
 
     def step(self, nsteps=1):
@@ -133,18 +173,18 @@ class Handle:
     def fields(self, rho=None, ux=None, uy=None, T=None, on_device=False):
         if not on_device and rho is None and ux is None and uy is None and T is None:
             rho, ux, uy, T = (np.empty(self.shape) for _ in range(4))
-        a = [_addr(v, on_device) for v in (rho, ux, uy, T)]
+        a = [_addr(v, on_device, self.sites) for v in (rho, ux, uy, T)]
         self._check(_lib.fftlb_fields(self._h, *a, int(on_device)))
         return rho, ux, uy, T
 
     def get_f(self, out=None, on_device=False):
         if out is None:
             out = np.empty((33,) + self.shape)
-        self._check(_lib.fftlb_get_f(self._h, _addr(out, on_device), int(on_device)))
+        self._check(_lib.fftlb_get_f(self._h, _addr(out, on_device, 33 * self.sites), int(on_device)))
         return out
 
     def set_f(self, f, on_device=False):
-        self._check(_lib.fftlb_set_f(self._h, _addr(f, on_device), int(on_device)))
+        self._check(_lib.fftlb_set_f(self._h, _addr(f, on_device, 33 * self.sites), int(on_device)))
 
     def invariants(self):
         out = (ct.c_double * 6)()
@@ -153,7 +193,8 @@ class Handle:
 
     def gradient(self, g, out, nfields):
         """g, out: device addresses (fp64 [nfields][ny][nx] and [2 nfields][ny][nx])."""
-        self._check(_lib.fftlb_gradient(self._h, _addr(g, True), _addr(out, True), int(nfields)))
+        n = self.sites * int(nfields)
+        self._check(_lib.fftlb_gradient(self._h, _addr(g, True, n), _addr(out, True, 2 * n), int(nfields)))
 
     def save(self, path):
         self._check(_lib.fftlb_save(self._h, path.encode()))
@@ -175,6 +216,17 @@ class Handle:
         self._check(_lib.fftlb_profile_read(self._h, ms, n, by, 6))
         return {_lib.fftlb_kernel_name(k).decode(): (ms[k], n[k], by[k]) for k in range(6)}
 
+    def autotune(self):
+        """fftlb_autotune: returns the best stage time in ms."""
+        ms = ct.c_double(0)
+        self._check(_lib.fftlb_autotune(self._h, ct.byref(ms)))
+        return ms.value
+
+    def tuning(self, values=None):
+        t = (ct.c_int * 5)(*(values or [0] * 5))
+        self._check(_lib.fftlb_tuning(self._h, t, 0 if values is None else 1))
+        return list(t)
+
     def close(self):
         if self._h:
             _lib.fftlb_destroy(self._h)
@@ -193,10 +245,87 @@ class Handle:
         self.close()
 
 
+class Batch:
+    """Owning wrapper of an fftlb_batch_t (batched sweep of independent runs)."""
+
+    def __init__(self, params_list, speeds=None, autotune=True, stream=0):
+        self._h = _h()
+        n = len(params_list)
+        arr = (fftlb_params * n)(*params_list)
+        vs = None
+        if speeds is not None:
+            sp = (ct.c_double * 4)(*speeds)
+            self._speeds = sp
+            vs = ct.byref(fftlb_velset(4, ct.cast(sp, ct.POINTER(ct.c_double)), 8))
+        self.params = list(params_list)
+        st = _lib.fftlb_batch_create(ct.byref(self._h), n, arr, vs, int(bool(autotune)), ct.c_void_p(int(stream)))
+        if st != OK:
+            raise FFTLBError(st, _lib.fftlb_last_error(None).decode())
+
+    def _check(self, st):
+        if st != OK:
+            raise FFTLBError(st, _lib.fftlb_batch_last_error(self._h).decode())
+
+    def __len__(self):
+        return len(self.params)
+
+    def shape(self, run):
+        p = self.params[run]
+        return (p.ny, p.nx)
+
+    def set_fields(self, run, rho, ux, uy, T, on_device=False):
+        ny, nx = self.shape(run)
+        a = [_addr(v, on_device, nx * ny) for v in (rho, ux, uy, T)]
+        self._check(_lib.fftlb_batch_set_fields(self._h, int(run), *a, int(on_device)))
+
+    def step(self, nsteps=1):
+        self._check(_lib.fftlb_batch_step(self._h, int(nsteps)))
+
+    def fields(self, run):
+        out = [np.empty(self.shape(run)) for _ in range(4)]
+        self._check(_lib.fftlb_batch_fields(self._h, int(run), *[_addr(v, False) for v in out], 0))
+        return out
+
+    def get_f(self, run):
+        out = np.empty((33,) + self.shape(run))
+        self._check(_lib.fftlb_batch_get_f(self._h, int(run), _addr(out, False), 0))
+        return out
+
+    def invariants(self, run):
+        out = (ct.c_double * 6)()
+        self._check(_lib.fftlb_batch_invariants(self._h, int(run), out))
+        return dict(mass=out[0], px=out[1], py=out[2], eT=out[3], umax=out[4], time=out[5])
+
+    def tuning(self, run):
+        t = (ct.c_int * 5)()
+        self._check(_lib.fftlb_batch_tuning(self._h, int(run), t))
+        return list(t)
+
+    def launches_per_step(self):
+        return _lib.fftlb_batch_launches_per_step(self._h)
+
+    def close(self):
+        if self._h:
+            _lib.fftlb_batch_destroy(self._h)
+            self._h = _h()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 def gradient_static(g, out, nx, ny, dx=1.0 / 256, window=4, stream=0):
     """fftlb_gradient_static: D_x, D_y of one fp64 device field without any
     device allocation (g, out: device addresses of [ny][nx] and [2][ny][nx])."""
-    st = _lib.fftlb_gradient_static(_addr(g, True), _addr(out, True), int(nx), int(ny), float(dx),
+    st = _lib.fftlb_gradient_static(_addr(g, True, nx * ny), _addr(out, True, 2 * nx * ny), int(nx), int(ny), float(dx),
                                     int(window), ct.c_void_p(int(stream)))
     if st != OK:
         raise FFTLBError(st, _lib.fftlb_last_error(None).decode())

@@ -102,3 +102,13 @@ def smooth_random(nx, ny, seed=0, rho0=1.0, T0=0.9, amp=0.05, umax=0.02, modes=3
     uy = umax * field()
     T = T0 * (1.0 + 0.5 * amp * field())
     return rho, ux, uy, T
+
+
+def sweep_plan(nruns=64, seed=3, sizes=(128, 256, 384, 512), tr_range=(0.70, 0.99)):
+    """Phase-diagram sweep: for each run a square grid drawn from `sizes` and
+    a reduced temperature drawn uniformly from `tr_range` (numpy PCG64,
+    one generator for the whole plan).  Returns [(n, T_r), ...]."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=nruns)
+    trs = rng.uniform(tr_range[0], tr_range[1], size=nruns)
+    return [(int(n), float(t)) for n, t in zip(ns, trs)]

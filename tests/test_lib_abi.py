@@ -59,3 +59,18 @@ def test_null_handle_calls_return_arg_error(fl):
     assert lib.fftlb_step(None, 1, None) == fl.ERR_ARG
     assert lib.fftlb_invariants(None, None) == fl.ERR_ARG
     assert lib.fftlb_destroy(None) == fl.OK
+
+
+def test_binding_rejects_wrongly_sized_host_buffers(fl):
+    """The binding checks dtype, layout and element count of host buffers
+    before any pointer reaches the C calls."""
+    import numpy as np
+    fftlb = fl
+    a = np.zeros(12)
+    assert fftlb._addr(a, False, 12) == a.ctypes.data
+    with pytest.raises(ValueError):
+        fftlb._addr(np.zeros(12), False, 16)
+    with pytest.raises(TypeError):
+        fftlb._addr(np.zeros(16, dtype=np.float32), False, 16)
+    with pytest.raises(TypeError):
+        fftlb._addr(np.zeros((4, 8))[:, ::2], False, 16)

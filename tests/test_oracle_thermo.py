@@ -61,7 +61,7 @@ def test_sigma_matches_paper_theory_values():
     """Sec. 4.2: theoretical sigma at T = 0.95 for K = 7.5e-6 and 5e-6 (three
     significant digits); for K = 1e-5 the printed theory value 1.96e-4 does
     not follow the sqrt(K) scaling of the other two, while the printed
-    simulation value 1.98e-4 does (reading: a misprint, see DESIGN)."""
+    simulation value 1.98e-4 does (read as a misprint in the paper)."""
     g = golden()["laplace_sigma_T095"]
     for K, s_theory in zip(g["K"][1:], g["sigma_theory"][1:]):
         assert TH.sigma_square_gradient(0.95, 9 / 8, 1 / 3, K) == pytest.approx(s_theory, abs=0.006e-4)
