@@ -513,16 +513,19 @@ __global__ void __launch_bounds__(NT) k_row_final(const typename cplx_of<real>::
 template <typename real>
 __global__ void k_feq_init(const double *rho_g, const double *ux_g, const double *uy_g, const double *T_g,
                            real *f, size_t N) {
+    // (evaluated in fp64 for either storage type: the weight polynomial of
+    // the fastest ring cancels to ~1e-5 relative in fp32, and the initial
+    // state should carry only the final rounding)
     for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < N; s += (size_t)gridDim.x * blockDim.x) {
-        const real rho = (real)rho_g[s], ux = (real)ux_g[s], uy = (real)uy_g[s], T = (real)T_g[s];
-        real F[5];
-        weights_Fk<real>(T, F);
-        const real u2 = ux * ux + uy * uy, iT = real(1) / T, qq = real(0.5) * u2 * iT, om = real(1) - qq;
-        const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
-        const real p3 = iT * iT * iT / real(6), p4 = iT * iT * iT * iT / real(24);
+        const double rho = rho_g[s], ux = ux_g[s], uy = uy_g[s], T = T_g[s];
+        double F[5];
+        weights_Fk<double>(T, F);
+        const double u2 = ux * ux + uy * uy, iT = 1.0 / T, qq = 0.5 * u2 * iT, om = 1.0 - qq;
+        const double p0 = om + 0.5 * qq * qq, p1 = om * iT, p2 = 0.5 * om * iT * iT;
+        const double p3 = iT * iT * iT / 6.0, p4 = iT * iT * iT * iT / 24.0;
         for (int i = 0; i < Q; ++i) {
-            const real vu = VX<real>(i) * ux + VY<real>(i) * uy;
-            f[(size_t)i * N + s] = rho * F[c_ring[i]] * (p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4))));
+            const double vu = VX<double>(i) * ux + VY<double>(i) * uy;
+            f[(size_t)i * N + s] = (real)(rho * F[c_ring[i]] * (p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4)))));
         }
     }
 }
