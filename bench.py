@@ -83,8 +83,57 @@ def ncu_traffic(kernel, precision, n):
     return None
 
 
+_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024.0, "MB": 1024.0 ** 2, "GB": 1024.0 ** 3}
+
+
+def write_ncu_traffic(csv_path, precision, n, note):
+    """Writes profiles/ncu_traffic.txt from an ncu --csv log of one SSP-RK3
+    step of the pipelined kernels captured with the metrics
+    dram__bytes_read.sum and dram__bytes_write.sum: DRAM bytes per launch of
+    each kernel kind, averaged over its launches (the two multi-group column
+    launches of a stage alternate: level 1, then level 2)."""
+    import csv
+    rows = [ln for ln in open(csv_path) if ln.startswith('"')]
+    per = {}
+    for r in csv.DictReader(rows):
+        if r["Metric Name"] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        by = float(r["Metric Value"].replace(",", "")) * _UNITS.get(r["Metric Unit"], 1.0)
+        per.setdefault(int(r["ID"]), [r["Kernel Name"], 0.0])[1] += by
+    out, multi = {}, 0
+    for i in sorted(per):
+        name, by = per[i]
+        if "k1_pipe" in name:
+            k = "row_forward_moments"
+        elif "k3_pipe" in name:
+            k = "row_level1"
+        elif "k5_pipe" in name:
+            k = "row_final"
+        elif "kcol_pipe" in name:
+            if "false" in name or ", 0>" in name:
+                k = "col_convection"
+            else:
+                k = "col_level1" if multi % 2 == 0 else "col_level2"
+                multi += 1
+        else:
+            continue
+        out.setdefault(k, []).append(by)
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    with open(path, "w") as fh:
+        fh.write("# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), averaged over the\n"
+                 "# launches of one SSP-RK3 step; valid for the kernel sources with this hash only.\n"
+                 "# kernel precision grid bytes_per_launch source_hash launches note\n")
+        for k, v in out.items():
+            fh.write("%s %d %d %.0f %s %d %s\n" % (k, precision, n, sum(v) / len(v), source_hash(), len(v), note))
+    return out
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms from
+    before the warm-up to after the profiled pass; summary() keeps the
+    samples taken inside the timed region, or, when that region is shorter
+    than three sampling periods, those of the whole busy window around it
+    (warm-up, timed steps, profiled steps), and says which."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -96,17 +145,18 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.5)   # let the first samples arrive before the GPU work starts
         except (OSError, ValueError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -116,10 +166,15 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0, t1, busy0, busy1):
+        def pick(a, b):
+            return [ln for t, ln in self.lines if a <= t <= b]
+        window, lines = "timed", pick(t0, t1)
+        if len(lines) < 3:
+            window, lines = "busy window around the timed region", pick(busy0, busy1)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 6:
                 continue
@@ -132,9 +187,9 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "window": window}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": window}
 
 
 def cpu_baseline(n=1024):
@@ -180,7 +235,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -188,9 +243,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 companion measurement")
+    ap.add_argument("--ncu-traffic-from", default=None, metavar="CSV",
+                    help="write profiles/ncu_traffic.txt from an ncu --csv log of one step (no GPU work)")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the batched sweep (64 runs of uneven grids replayed as one CUDA graph)")
     args = ap.parse_args()
+    if args.ncu_traffic_from:
+        res = write_ncu_traffic(args.ncu_traffic_from, args.precision, args.grid,
+                                "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum")
+        print(json.dumps({k: sum(v) / len(v) for k, v in res.items()}))
+        return
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -227,23 +289,24 @@ def main():
         return float(t.item())
 
     def time_path(precision, steps, warmup, sample_clocks):
+        clk = ClockSampler(local)
+        if sample_clocks:
+            clk.__enter__()
         h = fftlb.Handle(workload_params(fftlb, n, precision), stream=stream.cuda_stream)
         h.set_fields(*fields)
+        busy0 = time.perf_counter()
         h.step(warmup)
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
-        clk = ClockSampler(local)
-        if sample_clocks:
-            clk.__enter__()
+        t0 = time.perf_counter()
         ev0.record(stream)
         h.step(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-        if sample_clocks:
-            clk.__exit__()
+        t1 = time.perf_counter()
         barrier()
         ms = maxed(ev0.elapsed_time(ev1))
         # per-kernel timing on a second pass of the same length
@@ -251,10 +314,13 @@ def main():
         h.step(steps)
         prof = h.profile_read()
         h.profile(False)
+        busy1 = time.perf_counter()
+        if sample_clocks:
+            clk.__exit__()
         inv = h.invariants()
         lps = h.launches_per_step()
         h.close()
-        return ms, prof, inv, lps, (clk.summary() if sample_clocks else None)
+        return ms, prof, inv, lps, (clk.summary(t0, t1, busy0, busy1) if sample_clocks else None)
 
     ms, prof, inv, lps, clocks = time_path(args.precision, args.steps, args.warmup, True)
     K = args.steps
