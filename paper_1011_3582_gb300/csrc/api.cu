@@ -37,6 +37,7 @@ namespace fftlb {
 // lets handle-less entry points in other translation units report a message
 // through fftlb_last_error(NULL)
 void set_handleless_error(const std::string &msg) { g_create_err = msg; }
+Engine *engine_of(fftlb_t h) { return h ? h->eng : nullptr; }
 
 const char *const kKernelNames[KK_COUNT] = {"row_forward_moments", "col_convection", "col_level1",
                                             "row_level1",          "col_level2",     "row_final"};

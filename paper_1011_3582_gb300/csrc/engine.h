@@ -71,4 +71,8 @@ extern const char *const kKernelNames[KK_COUNT];
 Engine *make_engine_f64();
 Engine *make_engine_f32();
 
+// the engine behind a handle (NULL for a NULL handle); defined in api.cu
+Engine *engine_of(fftlb_t h);
+void set_handleless_error(const std::string &msg);
+
 }  // namespace fftlb

@@ -30,7 +30,12 @@ EXPORTED = ["fftlb_create", "fftlb_set_fields", "fftlb_step", "fftlb_fields", "f
             "fftlb_profile_read", "fftlb_kernel_name", "fftlb_gradient_static", "fftlb_autotune",
             "fftlb_tuning", "fftlb_batch_create", "fftlb_batch_set_fields", "fftlb_batch_step",
             "fftlb_batch_fields", "fftlb_batch_get_f", "fftlb_batch_invariants", "fftlb_batch_tuning",
-            "fftlb_batch_launches_per_step", "fftlb_batch_destroy", "fftlb_batch_last_error"]
+            "fftlb_batch_launches_per_step", "fftlb_batch_destroy", "fftlb_batch_last_error",
+            "fftlb_cnn_create", "fftlb_cnn_destroy", "fftlb_cnn_last_error", "fftlb_cnn_set_params",
+            "fftlb_cnn_get_params", "fftlb_cnn_forward", "fftlb_cnn_gradient", "fftlb_cnn_train_step",
+            "fftlb_cnn_encode", "fftlb_cnn_warm_start", "fftlb_cnn_launches"]
+
+CNN_NPARAMS = 32 * 9 * 3 + 32 + 32 * 9 * 32 + 32 + 32 * 9 * 32 + 32 + 2 * 9 * 32 + 2
 
 
 class fftlb_params(ct.Structure):
@@ -243,6 +248,140 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+class fftlb_cnn_norm(ct.Structure):
+    _fields_ = [("rho_c", ct.c_double), ("T_c", ct.c_double), ("s_rho", ct.c_double), ("s_T", ct.c_double)]
+
+
+_lib.fftlb_cnn_create.argtypes = [ct.POINTER(_h), ct.c_int, ct.c_int, _p]
+_lib.fftlb_cnn_destroy.argtypes = [_h]
+_lib.fftlb_cnn_last_error.argtypes = [_h]
+_lib.fftlb_cnn_last_error.restype = ct.c_char_p
+_lib.fftlb_cnn_set_params.argtypes = [_h, _p, ct.c_int]
+_lib.fftlb_cnn_get_params.argtypes = [_h, _p]
+_lib.fftlb_cnn_forward.argtypes = [_h, _p, _p, ct.c_int]
+_lib.fftlb_cnn_gradient.argtypes = [_h, _p, _p, _p, ct.POINTER(ct.c_double), ct.c_int]
+_lib.fftlb_cnn_train_step.argtypes = [_h, _p, _p, ct.c_float, ct.POINTER(ct.c_double), ct.c_int]
+_lib.fftlb_cnn_encode.argtypes = [_h, _h, ct.c_double, ct.POINTER(fftlb_cnn_norm), _p]
+_lib.fftlb_cnn_warm_start.argtypes = [_h, _h, ct.c_double, ct.POINTER(fftlb_cnn_norm)]
+_lib.fftlb_cnn_launches.argtypes = [_h]
+_lib.fftlb_cnn_launches.restype = ct.c_long
+
+
+def _faddr(x, on_device, count):
+    """Address of a float32 buffer (numpy on the host, torch on the device)."""
+    if on_device:
+        if isinstance(x, int):
+            return x
+        import torch
+        if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+            raise TypeError("device buffers must be contiguous float32 CUDA tensors")
+        if x.numel() != count:
+            raise ValueError(f"device buffer has {x.numel()} elements, expected {count}")
+        return int(x.data_ptr())
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float32 and x.flags.c_contiguous):
+        raise TypeError("host buffers must be C-contiguous float32 numpy arrays")
+    if x.size != count:
+        raise ValueError(f"host buffer has {x.size} elements, expected {count}")
+    return x.ctypes.data
+
+
+class CNN:
+    """Owning wrapper of an fftlb_cnn_t (the learned warm start)."""
+
+    def __init__(self, H, W, stream=0):
+        self._h = _h()
+        self.H, self.W = int(H), int(W)
+        st = _lib.fftlb_cnn_create(ct.byref(self._h), self.H, self.W, ct.c_void_p(int(stream)))
+        if st != OK:
+            raise FFTLBError(st, _lib.fftlb_last_error(None).decode())
+
+    def _check(self, st):
+        if st != OK:
+            raise FFTLBError(st, _lib.fftlb_cnn_last_error(self._h).decode())
+
+    @property
+    def P(self):
+        return self.H * self.W
+
+    def set_params(self, params, reset_optimizer=True):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != CNN_NPARAMS:
+            raise ValueError(f"expected {CNN_NPARAMS} parameters")
+        self._check(_lib.fftlb_cnn_set_params(self._h, a.ctypes.data, int(bool(reset_optimizer))))
+
+    def get_params(self):
+        a = np.empty(CNN_NPARAMS, np.float32)
+        self._check(_lib.fftlb_cnn_get_params(self._h, a.ctypes.data))
+        return a
+
+    def forward(self, X, Y=None, on_device=False):
+        if Y is None and not on_device:
+            Y = np.empty((2, self.H, self.W), np.float32)
+        self._check(_lib.fftlb_cnn_forward(self._h, _faddr(X, on_device, 3 * self.P),
+                                           _faddr(Y, on_device, 2 * self.P), int(on_device)))
+        return Y
+
+    def gradient(self, X, Xt, on_device=False):
+        g = np.empty(CNN_NPARAMS, np.float32)
+        loss = ct.c_double(0)
+        self._check(_lib.fftlb_cnn_gradient(self._h, _faddr(X, on_device, 3 * self.P),
+                                            _faddr(Xt, on_device, 2 * self.P), g.ctypes.data, ct.byref(loss),
+                                            int(on_device)))
+        return loss.value, g
+
+    def train_step(self, X, Xt, lr, on_device=False, want_loss=True):
+        loss = ct.c_double(0)
+        self._check(_lib.fftlb_cnn_train_step(self._h, _faddr(X, on_device, 3 * self.P),
+                                              _faddr(Xt, on_device, 2 * self.P), float(lr),
+                                              ct.byref(loss) if want_loss else None, int(on_device)))
+        return loss.value if want_loss else None
+
+    def encode(self, handle, T_run, norm, X_dev):
+        self._check(_lib.fftlb_cnn_encode(self._h, handle._h, float(T_run), ct.byref(norm),
+                                          _faddr(X_dev, True, 3 * self.P)))
+
+    def warm_start(self, handle, T_run, norm):
+        self._check(_lib.fftlb_cnn_warm_start(self._h, handle._h, float(T_run), ct.byref(norm)))
+
+    def launches(self):
+        return _lib.fftlb_cnn_launches(self._h)
+
+    def close(self):
+        if self._h:
+            _lib.fftlb_cnn_destroy(self._h)
+            self._h = _h()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def pack_params(params):
+    """Flatten [(W_l [out, 3, 3, in], b_l [out]), ...] into the fp32 vector
+    of the C ABI (W_1, b_1, W_2, b_2, ...)."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64).ravel()])
+                           for W, b in params]).astype(np.float32)
+
+
+def unpack_params(vec, layers=((3, 32), (32, 32), (32, 32), (32, 2))):
+    out, o = [], 0
+    for ci, co in layers:
+        W = np.asarray(vec[o:o + co * 9 * ci], np.float64).reshape(co, 3, 3, ci)
+        o += co * 9 * ci
+        b = np.asarray(vec[o:o + co], np.float64)
+        o += co
+        out.append((W, b))
+    return out
 
 
 class Batch:

@@ -74,3 +74,21 @@ def test_binding_rejects_wrongly_sized_host_buffers(fl):
         fftlb._addr(np.zeros(16, dtype=np.float32), False, 16)
     with pytest.raises(TypeError):
         fftlb._addr(np.zeros((4, 8))[:, ::2], False, 16)
+
+
+def test_cnn_create_rejects_bad_grids_without_device_work(fl):
+    for H, W in ((0, 64), (16, 48), (16, 8192)):
+        with pytest.raises(fl.FFTLBError) as ei:
+            fl.CNN(H, W)
+        assert ei.value.status == fl.ERR_ARG
+
+
+def test_cnn_parameter_packing_round_trip(fl):
+    import numpy as np
+    from oracle import cnn_oracle as C
+    params = C.init_params(3)
+    vec = fl.pack_params(params)
+    assert vec.size == fl.CNN_NPARAMS
+    back = fl.unpack_params(vec.astype(np.float64))
+    for (W1, b1), (W2, b2) in zip(params, back):
+        assert np.allclose(W1, W2, rtol=1e-6, atol=1e-7) and np.allclose(b1, b2)
