@@ -140,3 +140,20 @@ def test_rejects_bad_grids(fl):
         with pytest.raises(fl.FFTLBError) as ei:
             fl.CNN(H, Wd)
         assert ei.value.status == fl.ERR_ARG
+
+
+def test_trained_warm_start_shortens_time_to_onset(fl):
+    """The committed parameters (trained by paper_1011_3582_gb300.warmstart on
+    512^2 snapshots at T_r = 0.6, 0.65, 0.7, 0.75) on an unseen seed and
+    temperature at 256^2: the warm-started run reaches the onset contrast
+    (std(rho) / rho_c >= 0.2) in fewer than 0.7 times the plain run's steps,
+    and both runs end phase-separated."""
+    import os
+    from paper_1011_3582_gb300 import warmstart as WS
+    params = np.load(os.path.join(os.path.dirname(fl.__file__), "warmstart_params.npy"))
+    with fl.CNN(256, 256) as net:
+        net.set_params(params)
+        r = WS.compare(fl, net, 256, 0.65, 23, max_steps=80000)
+    print(r)
+    assert r["cold_steps"] is not None and r["warm_steps"] is not None
+    assert r["warm_steps"] <= 0.7 * r["cold_steps"]
