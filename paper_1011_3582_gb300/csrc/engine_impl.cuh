@@ -1371,11 +1371,33 @@ class EngineT : public Engine {
     }
 
     size_t budget_ = 0;
+    static constexpr int NT1 = KCfg<real, KS_K1>::NT, NTC = KCfg<real, KS_COL>::NT, NT5 = KCfg<real, KS_K5>::NT;
+    static int smax_for(int nx, int nt, int cap) {
+        const int s = (nx + nt - 1) / nt;
+        int r = 1;
+        while (r < s) r *= 2;
+        return r <= cap ? r : 0;
+    }
+    Status occ_k1(size_t sm, int *nb) {
+        switch (SMAX1_) {
+        case 1: return occupancy(k1_pipe<real, 1>, NT1, sm, nb);
+        case 2: return occupancy(k1_pipe<real, 2>, NT1, sm, nb);
+        case 4: return occupancy(k1_pipe<real, 4>, NT1, sm, nb);
+        default: return occupancy(k1_pipe<real, 8>, NT1, sm, nb);
+        }
+    }
+    Status occ_k5(size_t sm, int *nb) {
+        switch (SMAX5_) {
+        case 1: return occupancy(k5_pipe<real, 1>, NT5, sm, nb);
+        case 2: return occupancy(k5_pipe<real, 2>, NT5, sm, nb);
+        default: return occupancy(k5_pipe<real, 4>, NT5, sm, nb);
+        }
+    }
+
 
     Status configure_pipe(size_t budget) {
         budget_ = budget;
         const size_t cs = sizeof(C), rs = sizeof(real);
-        constexpr int NT = KCfg<real>::NT;
         if (((size_t)nx_ * rs) % 16 != 0)
             return Status::err(FFTLB_ERR_ARG, "rows must be a multiple of 16 bytes (fp32 needs nx divisible by 4)");
         int dev = 0;
@@ -1384,9 +1406,9 @@ class EngineT : public Engine {
         Status st;
         int nb = 0;
         const size_t ph = (size_t)padded_len(h_);
-        SMAX1_ = (nx_ + NT - 1) / NT;
-        SMAX1_ = SMAX1_ <= 1 ? 1 : (SMAX1_ <= 2 ? 2 : 4);
-        SMAX5_ = SMAX1_;
+        SMAX1_ = smax_for(nx_, NT1, 8);
+        SMAX5_ = smax_for(nx_, NT5, 4);
+        if (!SMAX1_ || !SMAX5_) return Status::err(FFTLB_ERR_ARG, "grid row too long for the row kernels");
         // K1: chunks of 6..8 rows (>= 6 for the level-1 rows); most blocks
         // per SM first, then the largest chunk
         {
@@ -1396,9 +1418,7 @@ class EngineT : public Engine {
                 const size_t sm =
                     smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ch * nx_ * rs, (size_t)ch * nx_ * rs, ch * ph * cs});
                 if (sm > budget) continue;
-                if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, sm, &nb);
-                else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, sm, &nb);
-                else st = occupancy(k1_pipe<real, 4>, NT, sm, &nb);
+                st = occ_k1(sm, &nb);
                 if (!st.good()) return st;
                 if (nb > bestnb) {
                     bestnb = nb;
@@ -1407,9 +1427,7 @@ class EngineT : public Engine {
                 }
             }
             if (!CH1_) return Status::err(FFTLB_ERR_ARG, "grid too large for the row kernel");
-            if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, smem1_, &nb);
-            else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, smem1_, &nb);
-            else st = occupancy(k1_pipe<real, 4>, NT, smem1_, &nb);
+            st = occ_k1(smem1_, &nb);
             if (!st.good()) return st;
             grid1_ = std::min(ny_, std::max(1, nb) * nsm_);
         }
@@ -1433,8 +1451,8 @@ class EngineT : public Engine {
                 const size_t sm = multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, 2 * tile, 2 * tile, ptile, ptile})
                                         : smem_bytes({ny_ * cs, ntc_ * cs, kt, tile, tile, ptile});
                 if (sm > budget) continue;
-                Status s2 = multi ? occupancy(kcol_pipe<real, true>, NT, sm, &nb)
-                                  : occupancy(kcol_pipe<real, false>, NT, sm, &nb);
+                Status s2 = multi ? occupancy(kcol_pipe<real, true>, NTC, sm, &nb)
+                                  : occupancy(kcol_pipe<real, false>, NTC, sm, &nb);
                 if (!s2.good()) return s2;
                 if (nb > bestnb) {
                     bestnb = nb;
@@ -1443,8 +1461,8 @@ class EngineT : public Engine {
                 }
             }
             if (!*tw_out) return Status::err(FFTLB_ERR_ARG, "grid too large for the column kernel");
-            Status s3 = multi ? occupancy(kcol_pipe<real, true>, NT, *sm_out, &nb)
-                              : occupancy(kcol_pipe<real, false>, NT, *sm_out, &nb);
+            Status s3 = multi ? occupancy(kcol_pipe<real, true>, NTC, *sm_out, &nb)
+                              : occupancy(kcol_pipe<real, false>, NTC, *sm_out, &nb);
             *grid_out = std::max(1, nb) * nsm_;
             return s3;
         };
@@ -1476,9 +1494,7 @@ class EngineT : public Engine {
                         smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
                                     (size_t)ch * nx_ * rs, (size_t)std::max(ch, 3) * ph * cs});
                     if (sm > budget) continue;
-                    if (SMAX5_ == 1) st = occupancy(k5_pipe<real, 1>, NT, sm, &nb);
-                    else if (SMAX5_ == 2) st = occupancy(k5_pipe<real, 2>, NT, sm, &nb);
-                    else st = occupancy(k5_pipe<real, 4>, NT, sm, &nb);
+                    st = occ_k5(sm, &nb);
                     if (!st.good()) return st;
                     const int score = nb * 100 + nhb * 10 + ch;
                     if (nb > 0 && score > bestscore) {
@@ -1491,9 +1507,7 @@ class EngineT : public Engine {
             }
         }
         if (!CH5_) return Status::err(FFTLB_ERR_ARG, "grid too large for the final row kernel");
-        if (SMAX5_ == 1) st = occupancy(k5_pipe<real, 1>, NT, smem5_, &nb);
-        else if (SMAX5_ == 2) st = occupancy(k5_pipe<real, 2>, NT, smem5_, &nb);
-        else st = occupancy(k5_pipe<real, 4>, NT, smem5_, &nb);
+        st = occ_k5(smem5_, &nb);
         if (!st.good()) return st;
         grid5_ = std::min(ny_, std::max(1, nb) * nsm_);
         return Status::ok();
@@ -1530,7 +1544,6 @@ class EngineT : public Engine {
     // grids and tensor maps; rejects values that do not fit
     Status set_tuning(const int t[NTUNE]) override {
         const size_t cs = sizeof(C), rs = sizeof(real);
-        constexpr int NT = KCfg<real>::NT;
         const size_t ph = (size_t)padded_len(h_), pny = (size_t)padded_len(ny_);
         const int twc = t[0] ? t[0] : TWc_, twl = t[1] ? t[1] : TWl_, ch1 = t[2] ? t[2] : CH1_;
         const int ch5 = t[3] ? t[3] : CH5_, nhb = t[4] ? t[4] : NHB5_;
@@ -1550,18 +1563,14 @@ class EngineT : public Engine {
             return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
         Status st;
         int nb = 0;
-        if (SMAX1_ == 1) st = occupancy(k1_pipe<real, 1>, NT, sm1, &nb);
-        else if (SMAX1_ == 2) st = occupancy(k1_pipe<real, 2>, NT, sm1, &nb);
-        else st = occupancy(k1_pipe<real, 4>, NT, sm1, &nb);
+        st = occ_k1(sm1, &nb);
         if (!st.good()) return st;
         const int g1 = std::min(ny_, std::max(1, nb) * nsm_);
-        if (!(st = occupancy(kcol_pipe<real, false>, NT, smc, &nb)).good()) return st;
+        if (!(st = occupancy(kcol_pipe<real, false>, NTC, smc, &nb)).good()) return st;
         const int gc = std::max(1, nb) * nsm_;
-        if (!(st = occupancy(kcol_pipe<real, true>, NT, sml, &nb)).good()) return st;
+        if (!(st = occupancy(kcol_pipe<real, true>, NTC, sml, &nb)).good()) return st;
         const int gl = std::max(1, nb) * nsm_;
-        if (SMAX5_ == 1) st = occupancy(k5_pipe<real, 1>, NT, sm5, &nb);
-        else if (SMAX5_ == 2) st = occupancy(k5_pipe<real, 2>, NT, sm5, &nb);
-        else st = occupancy(k5_pipe<real, 4>, NT, sm5, &nb);
+        st = occ_k5(sm5, &nb);
         if (!st.good()) return st;
         const int g5 = std::min(ny_, std::max(1, nb) * nsm_);
         CUtensorMap mc, ml;
@@ -1640,11 +1649,11 @@ class EngineT : public Engine {
   private:
     Status launch_col(int first, int count, bool level1) {
         if (level1)
-            kcol_pipe<real, true><<<gridl_, KCfg<real>::NT, smeml_, stream_>>>(spec_, groups_ + first, count, kxt_,
+            kcol_pipe<real, true><<<gridl_, NTC, smeml_, stream_>>>(spec_, groups_ + first, count, kxt_,
                                                                                kyt_, Wc_, Tc_, ntc_, kp_, TWl_, BOXR_,
                                                                                tmap_l1_, err_);
         else
-            kcol_pipe<real, false><<<gridc_, KCfg<real>::NT, smemc_, stream_>>>(
+            kcol_pipe<real, false><<<gridc_, NTC, smemc_, stream_>>>(
                 spec_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
         FFTLB_LAUNCHED("kcol_pipe");
         return Status::ok();
@@ -1654,14 +1663,15 @@ class EngineT : public Engine {
         Status st;
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
         if (SMAX1_ == 1)
-            k1_pipe<real, 1><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 1><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 2)
-            k1_pipe<real, 2><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 2><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
+        else if (SMAX1_ == 4)
+            k1_pipe<real, 4><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
         else
-            k1_pipe<real, 4><<<grid1_, KCfg<real>::NT, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
-                                                                                 CH1_, err_);
+            k1_pipe<real, 8><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
         FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
@@ -1679,13 +1689,13 @@ class EngineT : public Engine {
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         if (SMAX5_ == 1)
-            k5_pipe<real, 1><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 1><<<grid5_, NT5, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         else if (SMAX5_ == 2)
-            k5_pipe<real, 2><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 2><<<grid5_, NT5, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         else
-            k5_pipe<real, 4><<<grid5_, KCfg<real>::NT, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 4><<<grid5_, NT5, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         FFTLB_LAUNCHED("k5_pipe");
         return prof_end();

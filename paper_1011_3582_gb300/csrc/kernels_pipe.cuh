@@ -16,14 +16,32 @@
 
 #include "async_copy.cuh"
 
-#ifndef FFTLB_NT32
-#define FFTLB_NT32 512
+// Threads per block (NT) and minimum resident blocks per SM (MINB) of the
+// persistent kernels, per precision and kernel kind.  fp32 defaults
+// (measured at 1024^2): the row-forward kernel runs two 256-thread blocks
+// per SM (its 8-row chunks give one radix-16 butterfly per thread; 229 ->
+// 171 us), the column and final row kernels one 512-thread block (two
+// 256-thread blocks: convection columns 256 -> 348 us).
+#ifndef FFTLB_NT32_K1
+#define FFTLB_NT32_K1 256
+#endif
+#ifndef FFTLB_MINB32_K1
+#define FFTLB_MINB32_K1 2
+#endif
+#ifndef FFTLB_NT32_COL
+#define FFTLB_NT32_COL 512
+#endif
+#ifndef FFTLB_MINB32_COL
+#define FFTLB_MINB32_COL 1
+#endif
+#ifndef FFTLB_NT32_K5
+#define FFTLB_NT32_K5 512
+#endif
+#ifndef FFTLB_MINB32_K5
+#define FFTLB_MINB32_K5 1
 #endif
 #ifndef FFTLB_NT64
 #define FFTLB_NT64 256
-#endif
-#ifndef FFTLB_MINB32
-#define FFTLB_MINB32 1
 #endif
 #ifndef FFTLB_MINB64
 #define FFTLB_MINB64 1
@@ -50,15 +68,19 @@ inline size_t smem_bytes(std::initializer_list<size_t> parts) {
     return s;
 }
 
-// threads per block of the persistent kernels, per precision
-template <typename real> struct KCfg;
-template <> struct KCfg<float> {
-    static constexpr int NT = FFTLB_NT32;
-    static constexpr int MINB = FFTLB_MINB32;
+enum KernelShape { KS_K1 = 0, KS_COL = 1, KS_K5 = 2 };
+template <typename real, int KIND> struct KCfg;
+template <> struct KCfg<float, KS_K1> {
+    static constexpr int NT = FFTLB_NT32_K1, MINB = FFTLB_MINB32_K1;
 };
-template <> struct KCfg<double> {
-    static constexpr int NT = FFTLB_NT64;
-    static constexpr int MINB = FFTLB_MINB64;
+template <> struct KCfg<float, KS_COL> {
+    static constexpr int NT = FFTLB_NT32_COL, MINB = FFTLB_MINB32_COL;
+};
+template <> struct KCfg<float, KS_K5> {
+    static constexpr int NT = FFTLB_NT32_K5, MINB = FFTLB_MINB32_K5;
+};
+template <int KIND> struct KCfg<double, KIND> {
+    static constexpr int NT = FFTLB_NT64, MINB = FFTLB_MINB64;
 };
 
 template <typename C>
@@ -108,7 +130,7 @@ __device__ __forceinline__ void k1_issue(const real *f, real *dst, uint64_t *bar
 }
 
 template <typename real, int SMAX>
-__global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) k1_pipe(const real *__restrict__ f,
+__global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB) k1_pipe(const real *__restrict__ f,
                                                              typename cplx_of<real>::type *spec,
                                                              real *__restrict__ fields,
                                                              const typename cplx_of<real>::type *__restrict__ Wr_g,
@@ -116,7 +138,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) k1_pipe(cons
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
                                                              int ntr, KP<real> P, int CH, int *err) {
     using C = typename cplx_of<real>::type;
-    constexpr int NT = KCfg<real>::NT;
+    constexpr int NT = KCfg<real, KS_K1>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar0, bar1;
     const int nx = P.nx, ny = P.ny, h = P.h, tid = threadIdx.x;
@@ -337,7 +359,7 @@ __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDes
 // MULTI = false: every group has one input and one output in place
 // (convection); MULTI = true: up to 2 inputs and several outputs.
 template <typename real, bool MULTI>
-__global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) kcol_pipe(typename cplx_of<real>::type *spec,
+__global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MINB) kcol_pipe(typename cplx_of<real>::type *spec,
                                                                const GroupDesc *__restrict__ groups, int ngroups,
                                                                const real *__restrict__ kxt,
                                                                const real *__restrict__ kyt,
@@ -346,7 +368,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) kcol_pipe(ty
                                                                int ntc, KP<real> P, int TW, int BOXR,
                                                                const __grid_constant__ CUtensorMap tmap, int *err) {
     using C = typename cplx_of<real>::type;
-    constexpr int NT = KCfg<real>::NT;
+    constexpr int NT = KCfg<real, KS_COL>::NT;
     constexpr int NIN = MULTI ? 2 : 1;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar0, bar1;
@@ -604,7 +626,7 @@ __device__ __forceinline__ void k5_issue_head(const typename cplx_of<real>::type
 // NHB head buffers (1 or 2): the head of row ri lives in buffer ri % NHB and
 // is prefetched NHB rows ahead.
 template <typename real, int SMAX>
-__global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) k5_pipe(const typename cplx_of<real>::type *spec,
+__global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB) k5_pipe(const typename cplx_of<real>::type *spec,
                                                              const real *__restrict__ fields,
                                                              const real *__restrict__ aux, const real *fcur,
                                                              const real *fbase, real *fout, real alpha, real beta,
@@ -613,7 +635,7 @@ __global__ void __launch_bounds__(KCfg<real>::NT, KCfg<real>::MINB) k5_pipe(cons
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
                                                              int ntr, KP<real> P, int CH, int NHB, int *err) {
     using C = typename cplx_of<real>::type;
-    constexpr int NT = KCfg<real>::NT;
+    constexpr int NT = KCfg<real, KS_K5>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar0, bar1, hbar0, hbar1;
     const int nx = P.nx, ny = P.ny, h = P.h, tid = threadIdx.x;
