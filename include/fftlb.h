@@ -166,13 +166,15 @@ fftlb_status fftlb_autotune(fftlb_t h, double *stage_ms);
 fftlb_status fftlb_tuning(fftlb_t h, int tuning[5], int set);
 
 /* Batched sweep: nruns independent problems (each its own grid, parameters
- * and state; the same velocity set) advanced together.  One time step of
- * every run, the runs one after another on one internal stream, is
- * captured once into a CUDA graph; fftlb_batch_step(b, n) replays it n
- * times on cuda_stream (borrowed; NULL = legacy default stream).  With
- * autotune != 0, fftlb_batch_create tunes one run of every distinct
- * (nx, ny, precision, integrator) and applies its parameters to all runs of
- * that shape.  check_every is ignored (no host checks inside replays); call
+ * and state; the same velocity set) advanced together.  Runs with identical
+ * fftlb_params (check_every aside) form a group whose states are stored
+ * back to back; every kernel of a stage is one persistent launch over the
+ * rows / column tiles of all runs of the group.  One time step of every
+ * group, the groups one after another on one internal stream, is captured
+ * once into a CUDA graph; fftlb_batch_step(b, n) replays it n times on
+ * cuda_stream (borrowed; NULL = legacy default stream).  With autotune != 0,
+ * fftlb_batch_create tunes each group's launch parameters on a uniform
+ * state.  check_every is ignored (no host checks inside replays); call
  * fftlb_batch_invariants to inspect a run.  Per-run calls take the run
  * index; they are ordered after the steps already launched.  Results of a
  * run are identical to those of a single handle with the same parameters.

@@ -61,7 +61,7 @@ fftlb_status fftlb_create(fftlb_t *h, const fftlb_params *p, const fftlb_velset 
     fftlb_t hh = new (std::nothrow) fftlb_s();
     if (!hh) return fail(nullptr, FFTLB_ERR_OOM, "host allocation failed");
     hh->eng = p->precision == 64 ? fftlb::make_engine_f64() : fftlb::make_engine_f32();
-    fftlb::Status st = hh->eng->init(*p, speeds, reinterpret_cast<cudaStream_t>(stream));
+    fftlb::Status st = hh->eng->init(*p, speeds, reinterpret_cast<cudaStream_t>(stream), 1);
     if (!st.good()) {
         delete hh->eng;
         delete hh;

@@ -1,15 +1,15 @@
 // Batched sweep of independent FFT-LB runs (a phase-diagram sweep: many
-// grids and temperatures, arXiv:1011.3582 Sec. 4.1) advanced together: one
-// time step of every run, the runs one after another on one internal
-// stream, is captured once into a CUDA graph, and every fftlb_batch_step
-// replays the graph on the caller's stream (one graph launch per step
-// instead of 18 kernel launches per run).  The persistent kernels of one
-// run already spread over every SM, so the runs are not overlapped.  Runs
-// of the same grid shape and precision share the launch parameters picked
-// by the engine's autotuner.  Declarations and contracts: include/fftlb.h.
+// grids and temperatures, arXiv:1011.3582 Sec. 4.1) advanced together.
+// Runs that share every parameter (grid, dx, dt, tau, EOS, K, H, q, zeta,
+// window, integrator, precision) form one group, held by one engine whose
+// arenas store the group's runs back to back: each pipelined kernel of a
+// stage is one persistent launch over the rows or column tiles of all runs
+// of the group.  One time step of every group is captured once into a CUDA
+// graph on one internal stream (18 kernel nodes per group for SSP-RK3),
+// and every fftlb_batch_step replays the graph on the caller's stream.
+// Declarations and contracts: include/fftlb.h.
 #include <map>
 #include <string>
-#include <tuple>
 #include <vector>
 
 #include "engine.h"
@@ -19,8 +19,9 @@ void set_handleless_error(const std::string &msg);
 }
 
 struct fftlb_batch_s {
-    std::vector<fftlb::Engine *> eng;
-    cudaStream_t origin = nullptr;   // every run's stream and the capture stream (owned)
+    std::vector<fftlb::Engine *> eng;          // one per parameter group
+    std::vector<std::pair<int, int>> where;    // run -> (group, index in the group)
+    cudaStream_t origin = nullptr;   // every group's stream and the capture stream (owned)
     cudaStream_t user = nullptr;     // caller's stream (borrowed)
     cudaEvent_t ready = nullptr, done = nullptr;
     cudaGraph_t graph = nullptr;
@@ -113,49 +114,62 @@ fftlb_status fftlb_batch_create(fftlb_batch_t *out, int nruns, const fftlb_param
         cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
         return bad(FFTLB_ERR_CUDA, "stream / event creation failed");
-    std::map<std::tuple<int, int, int, int>, std::vector<int>> shapes;
+    // group runs whose parameters are identical (check_every is ignored:
+    // steps are graph replays, with no host-side checks inside)
+    std::map<std::string, std::vector<int>> groups;
+    std::vector<std::string> order;
     for (int r = 0; r < nruns; ++r) {
         fftlb_params p = params[r];
-        p.check_every = 0;   // steps are graph replays: no host-side checks inside
+        p.check_every = 0;
+        std::string key(reinterpret_cast<const char *>(&p), sizeof p);
+        if (!groups.count(key)) order.push_back(key);
+        groups[key].push_back(r);
+    }
+    b->where.assign(nruns, std::make_pair(0, 0));
+    for (size_t gi = 0; gi < order.size(); ++gi) {
+        const std::vector<int> &runs = groups[order[gi]];
+        fftlb_params p = params[runs[0]];
+        p.check_every = 0;
         fftlb::Engine *eng = p.precision == 64 ? fftlb::make_engine_f64() : fftlb::make_engine_f32();
         b->eng.push_back(eng);
-        fftlb::Status st = eng->init(p, speeds, b->origin);
-        if (!st.good()) return bad(st.code, "run " + std::to_string(r) + ": " + st.msg);
-        shapes[std::make_tuple(p.nx, p.ny, p.precision, p.integrator)].push_back(r);
-    }
-    if (autotune) {
-        // tune one run per shape on a uniform equilibrium state, share the choice
-        for (auto &kv : shapes) {
-            const int r0 = kv.second[0];
-            const fftlb_params &p = b->eng[r0]->params();
+        fftlb::Status st = eng->init(p, speeds, b->origin, (int)runs.size());
+        if (!st.good()) return bad(st.code, "run " + std::to_string(runs[0]) + ": " + st.msg);
+        for (size_t i = 0; i < runs.size(); ++i) b->where[runs[i]] = std::make_pair((int)gi, (int)i);
+        if (autotune) {
+            // tune on a uniform state (rho_c, 0.9 T_c) in every run of the group
             const size_t n = (size_t)p.nx * p.ny;
             std::vector<double> rho(n, 1.0 / (3.0 * (p.b > 0 ? p.b : 1.0 / 3.0))), z(n, 0.0);
             std::vector<double> T(n, p.b > 0 ? 0.9 * 8.0 * p.a / (27.0 * p.b) : 1.0);
-            fftlb::Status st = b->eng[r0]->set_fields(rho.data(), z.data(), z.data(), T.data(), false);
-            double ms = 0;
-            if (st.good()) st = b->eng[r0]->autotune(&ms);
-            if (!st.good()) return bad(st.code, "autotune: " + st.msg);
-            int t[fftlb::Engine::NTUNE];
-            b->eng[r0]->get_tuning(t);
-            for (int r : kv.second) {
-                st = b->eng[r]->set_tuning(t);
-                if (!st.good()) return bad(st.code, "autotune: " + st.msg);
+            for (size_t i = 0; i < runs.size() && st.good(); ++i) {
+                st = eng->select_run((int)i);
+                if (st.good()) st = eng->set_fields(rho.data(), z.data(), z.data(), T.data(), false);
             }
+            double ms = 0;
+            if (st.good()) st = eng->autotune(&ms);
+            if (!st.good()) return bad(st.code, "autotune: " + st.msg);
         }
     }
     *out = b;
     return FFTLB_OK;
 }
 
+// the engine holding a run, with that run selected (NULL if out of range)
+static fftlb::Engine *run_engine(fftlb_batch_t b, int run) {
+    if (run < 0 || run >= (int)b->where.size()) return nullptr;
+    fftlb::Engine *e = b->eng[b->where[run].first];
+    return e->select_run(b->where[run].second).good() ? e : nullptr;
+}
+
 fftlb_status fftlb_batch_set_fields(fftlb_batch_t b, int run, const double *rho, const double *ux, const double *uy,
                                     const double *T, int on_device) {
     if (!b) return fail(nullptr, FFTLB_ERR_ARG, "NULL batch");
-    if (run < 0 || run >= (int)b->eng.size()) return fail(b, FFTLB_ERR_ARG, "run out of range");
+    fftlb::Engine *e = run_engine(b, run);
+    if (!e) return fail(b, FFTLB_ERR_ARG, "run out of range");
     fftlb_status s = after_graph(b);
     if (s != FFTLB_OK) return s;
-    fftlb::Status st = b->eng[run]->set_fields(rho, ux, uy, T, on_device != 0);
+    fftlb::Status st = e->set_fields(rho, ux, uy, T, on_device != 0);
     if (!st.good()) return fail(b, st);
-    b->eng[run]->set_steps(b->steps);
+    e->set_steps(b->steps);
     return FFTLB_OK;
 }
 
@@ -177,35 +191,39 @@ fftlb_status fftlb_batch_step(fftlb_batch_t b, long nsteps) {
 fftlb_status fftlb_batch_fields(fftlb_batch_t b, int run, double *rho, double *ux, double *uy, double *T,
                                 int on_device) {
     if (!b) return fail(nullptr, FFTLB_ERR_ARG, "NULL batch");
-    if (run < 0 || run >= (int)b->eng.size()) return fail(b, FFTLB_ERR_ARG, "run out of range");
+    fftlb::Engine *e = run_engine(b, run);
+    if (!e) return fail(b, FFTLB_ERR_ARG, "run out of range");
     fftlb_status s = after_graph(b);
     if (s != FFTLB_OK) return s;
-    fftlb::Status st = b->eng[run]->fields(rho, ux, uy, T, on_device != 0);
+    fftlb::Status st = e->fields(rho, ux, uy, T, on_device != 0);
     return st.good() ? FFTLB_OK : fail(b, st);
 }
 
 fftlb_status fftlb_batch_get_f(fftlb_batch_t b, int run, double *f, int on_device) {
     if (!b) return fail(nullptr, FFTLB_ERR_ARG, "NULL batch");
-    if (run < 0 || run >= (int)b->eng.size()) return fail(b, FFTLB_ERR_ARG, "run out of range");
+    fftlb::Engine *e = run_engine(b, run);
+    if (!e) return fail(b, FFTLB_ERR_ARG, "run out of range");
     fftlb_status s = after_graph(b);
     if (s != FFTLB_OK) return s;
-    fftlb::Status st = b->eng[run]->get_f(f, on_device != 0);
+    fftlb::Status st = e->get_f(f, on_device != 0);
     return st.good() ? FFTLB_OK : fail(b, st);
 }
 
 fftlb_status fftlb_batch_invariants(fftlb_batch_t b, int run, double out[6]) {
     if (!b) return fail(nullptr, FFTLB_ERR_ARG, "NULL batch");
-    if (run < 0 || run >= (int)b->eng.size() || !out) return fail(b, FFTLB_ERR_ARG, "run out of range or out NULL");
+    fftlb::Engine *e = out ? run_engine(b, run) : nullptr;
+    if (!e) return fail(b, FFTLB_ERR_ARG, "run out of range or out NULL");
     fftlb_status s = after_graph(b);
     if (s != FFTLB_OK) return s;
-    fftlb::Status st = b->eng[run]->invariants(out);
+    fftlb::Status st = e->invariants(out);
     return st.good() ? FFTLB_OK : fail(b, st);
 }
 
 fftlb_status fftlb_batch_tuning(fftlb_batch_t b, int run, int tuning[5]) {
     if (!b) return fail(nullptr, FFTLB_ERR_ARG, "NULL batch");
-    if (run < 0 || run >= (int)b->eng.size() || !tuning) return fail(b, FFTLB_ERR_ARG, "run out of range or NULL");
-    b->eng[run]->get_tuning(tuning);
+    fftlb::Engine *e = tuning ? run_engine(b, run) : nullptr;
+    if (!e) return fail(b, FFTLB_ERR_ARG, "run out of range or NULL");
+    e->get_tuning(tuning);
     return FFTLB_OK;
 }
 

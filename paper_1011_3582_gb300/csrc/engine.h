@@ -26,7 +26,13 @@ struct Status {
 class Engine {
   public:
     virtual ~Engine() {}
-    virtual Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s) = 0;
+    // nrun independent runs of the same grid and parameters, advanced
+    // together by step / enqueue_step; per-run calls (set_fields, fields,
+    // get_f, set_f, invariants, gradient) act on the run chosen by
+    // select_run (run 0 after init)
+    virtual Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s, int nrun) = 0;
+    virtual Status select_run(int run) = 0;
+    virtual int nrun() const = 0;
     virtual Status set_fields(const double *rho, const double *ux, const double *uy, const double *T,
                               bool on_device) = 0;
     virtual Status step(long nsteps, long *done) = 0;

@@ -74,8 +74,12 @@ template <typename real> __device__ __forceinline__ real FKC(int k, int j);
 template <> __device__ __forceinline__ double FKC<double>(int k, int j) { return c_Fk[k][j]; }
 template <> __device__ __forceinline__ float FKC<float>(int k, int j) { return c_Fkf[k][j]; }
 
+// nrun: independent runs of this grid stored back to back (f [run][33][ny][nx],
+// spectra [run][58][ny][nx/2], fields [run][4][ny][nx], aux [run][3][ny][nx]);
+// the pipelined kernels treat the nrun * ny rows (or column tiles) of all
+// runs as one job list
 template <typename real> struct KP {
-    int nx, ny, h;
+    int nx, ny, h, nrun;
     real dx, dt, tau, a, b, K, H, q, zeta, scale;
 };
 
@@ -732,9 +736,11 @@ class EngineT : public Engine {
         release();
     }
 
-    Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s) override {
+    Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s, int nrun) override {
         p_ = p;
         stream_ = s;
+        if (nrun < 1 || nrun > 4096) return Status::err(FFTLB_ERR_ARG, "nrun must be in [1, 4096]");
+        B_ = nrun;
         const int maxn = sizeof(real) == 8 ? 1024 : 2048;
         if (!valid_len(p.nx) || !valid_len(p.ny) || p.nx > maxn || p.ny > maxn)
             return Status::err(FFTLB_ERR_ARG, "nx, ny must be even 2^p 3^q in [4, " + std::to_string(maxn) + "]");
@@ -778,11 +784,11 @@ class EngineT : public Engine {
         for (long n = 0; n < nsteps; ++n) {
             Status st;
             if (p_.integrator == 1) {
-                st = stage(f0_, nullptr, f0_, real(0), real(1));
+                st = stage(f0b_, nullptr, f0b_, real(0), real(1));
             } else {
-                st = stage(f0_, nullptr, f1_, real(0), real(1));
-                if (st.good()) st = stage(f1_, f0_, f1_, real(0.75), real(0.25));
-                if (st.good()) st = stage(f1_, f0_, f0_, real(1.0 / 3.0), real(2.0 / 3.0));
+                st = stage(f0b_, nullptr, f1b_, real(0), real(1));
+                if (st.good()) st = stage(f1b_, f0b_, f1b_, real(0.75), real(0.25));
+                if (st.good()) st = stage(f1b_, f0b_, f0b_, real(1.0 / 3.0), real(2.0 / 3.0));
             }
             if (!st.good()) return st;
             ++steps_;
@@ -871,6 +877,13 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
+    Status select_run(int run) override {
+        if (run < 0 || run >= B_) return Status::err(FFTLB_ERR_ARG, "run index out of range");
+        set_views(run);
+        return Status::ok();
+    }
+    int nrun() const override { return B_; }
+
     long steps() const override { return steps_; }
     void set_steps(long s) override { steps_ = s; }
     int launches_per_step() const override { return 6 * (p_.integrator == 1 ? 1 : 3); }
@@ -884,6 +897,10 @@ class EngineT : public Engine {
     long steps_ = 0;
     KP<real> kp_{};
     // device memory
+    // batch bases (B_ runs back to back) and the views of the selected run
+    int B_ = 1, run_ = 0;
+    real *f0b_ = nullptr, *f1b_ = nullptr, *fieldsb_ = nullptr, *auxb_ = nullptr;
+    C *specb_ = nullptr;
     real *f0_ = nullptr, *f1_ = nullptr, *fields_ = nullptr, *aux_ = nullptr;
     C *spec_ = nullptr;
     real *kxt_ = nullptr, *kyt_ = nullptr;
@@ -966,7 +983,7 @@ class EngineT : public Engine {
     Status profile_read(double *ms, long *launches, double *bytes, int nkinds) override {
         Status st = prof_flush();
         if (!st.good()) return st;
-        const double s = sizeof(real), NN = (double)N_;
+        const double s = sizeof(real), NN = (double)N_ * B_;   // all runs of one launch
         const double fbase = p_.integrator == 3 ? 2.0 / 3.0 : 0.0;   // stages 2, 3 read f^n
         // algorithmic bytes per launch: every value each kernel must read or
         // write once (one-sided spectra count N reals per field)
@@ -986,6 +1003,16 @@ class EngineT : public Engine {
     }
 
   private:
+
+    void set_views(int run) {
+        run_ = run;
+        const size_t r = (size_t)run;
+        f0_ = f0b_ + r * Q * N_;
+        f1_ = f1b_ ? f1b_ + r * Q * N_ : nullptr;
+        spec_ = specb_ + r * NSLOT * ny_ * h_;
+        fields_ = fieldsb_ + r * 4 * N_;
+        aux_ = auxb_ + r * 3 * N_;
+    }
 
     unsigned grid1d() const {
         size_t b = (N_ + 255) / 256;
@@ -1069,11 +1096,13 @@ class EngineT : public Engine {
 
     Status alloc() {
         Status st;
-        if (!(st = dalloc(&f0_, Q * N_)).good()) return st;
-        if (p_.integrator == 3 && !(st = dalloc(&f1_, Q * N_)).good()) return st;
-        if (!(st = dalloc(&spec_, (size_t)NSLOT * ny_ * h_)).good()) return st;
-        if (!(st = dalloc(&fields_, 4 * N_)).good()) return st;
-        if (!(st = dalloc(&aux_, 3 * N_)).good()) return st;
+        const size_t B = (size_t)B_;
+        if (!(st = dalloc(&f0b_, B * Q * N_)).good()) return st;
+        if (p_.integrator == 3 && !(st = dalloc(&f1b_, B * Q * N_)).good()) return st;
+        if (!(st = dalloc(&specb_, B * NSLOT * ny_ * h_)).good()) return st;
+        if (!(st = dalloc(&fieldsb_, B * 4 * N_)).good()) return st;
+        if (!(st = dalloc(&auxb_, B * 3 * N_)).good()) return st;
+        set_views(0);
         if (!(st = dalloc(&kxt_, (size_t)h_ + 1)).good()) return st;
         if (!(st = dalloc(&kyt_, (size_t)ny_)).good()) return st;
         if (!(st = dalloc(&Wr_, (size_t)h_)).good()) return st;
@@ -1318,6 +1347,7 @@ class EngineT : public Engine {
         kp_.nx = nx_;
         kp_.ny = ny_;
         kp_.h = h_;
+        kp_.nrun = B_;
         kp_.dx = (real)p_.dx;
         kp_.dt = (real)p_.dt;
         kp_.tau = (real)p_.tau;
@@ -1349,12 +1379,12 @@ class EngineT : public Engine {
     Status make_tmap(CUtensorMap *m, int TW) {
         auto enc = tensor_map_encoder();
         if (!enc) return Status::err(FFTLB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-        cuuint64_t dims[2] = {(cuuint64_t)(2 * h_), (cuuint64_t)NSLOT * ny_};
+        cuuint64_t dims[2] = {(cuuint64_t)(2 * h_), (cuuint64_t)B_ * NSLOT * ny_};
         cuuint64_t strides[1] = {(cuuint64_t)(2 * h_) * sizeof(real)};
         cuuint32_t box[2] = {(cuuint32_t)(2 * TW), (cuuint32_t)BOXR_};
         cuuint32_t es[2] = {1, 1};
         CUresult r = enc(m, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                         (void *)spec_, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         (void *)specb_, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return Status::err(FFTLB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -1429,7 +1459,7 @@ class EngineT : public Engine {
             if (!CH1_) return Status::err(FFTLB_ERR_ARG, "grid too large for the row kernel");
             st = occ_k1(smem1_, &nb);
             if (!st.good()) return st;
-            grid1_ = std::min(ny_, std::max(1, nb) * nsm_);
+            grid1_ = std::min(B_ * ny_, std::max(1, nb) * nsm_);
         }
         // column kernels: box height divides ny; most blocks per SM first,
         // then the widest tile
@@ -1509,7 +1539,7 @@ class EngineT : public Engine {
         if (!CH5_) return Status::err(FFTLB_ERR_ARG, "grid too large for the final row kernel");
         st = occ_k5(smem5_, &nb);
         if (!st.good()) return st;
-        grid5_ = std::min(ny_, std::max(1, nb) * nsm_);
+        grid5_ = std::min(B_ * ny_, std::max(1, nb) * nsm_);
         return Status::ok();
     }
 
@@ -1524,10 +1554,10 @@ class EngineT : public Engine {
   public:
     Status enqueue_step() override {
         Status st;
-        if (p_.integrator == 1) return stage(f0_, nullptr, f0_, real(0), real(1));
-        if (!(st = stage(f0_, nullptr, f1_, real(0), real(1))).good()) return st;
-        if (!(st = stage(f1_, f0_, f1_, real(0.75), real(0.25))).good()) return st;
-        return stage(f1_, f0_, f0_, real(1.0 / 3.0), real(2.0 / 3.0));
+        if (p_.integrator == 1) return stage(f0b_, nullptr, f0b_, real(0), real(1));
+        if (!(st = stage(f0b_, nullptr, f1b_, real(0), real(1))).good()) return st;
+        if (!(st = stage(f1b_, f0b_, f1b_, real(0.75), real(0.25))).good()) return st;
+        return stage(f1b_, f0b_, f0b_, real(1.0 / 3.0), real(2.0 / 3.0));
     }
 
     cudaStream_t stream() const override { return stream_; }
@@ -1565,14 +1595,14 @@ class EngineT : public Engine {
         int nb = 0;
         st = occ_k1(sm1, &nb);
         if (!st.good()) return st;
-        const int g1 = std::min(ny_, std::max(1, nb) * nsm_);
+        const int g1 = std::min(B_ * ny_, std::max(1, nb) * nsm_);
         if (!(st = occupancy(kcol_pipe<real, false>, NTC, smc, &nb)).good()) return st;
         const int gc = std::max(1, nb) * nsm_;
         if (!(st = occupancy(kcol_pipe<real, true>, NTC, sml, &nb)).good()) return st;
         const int gl = std::max(1, nb) * nsm_;
         st = occ_k5(sm5, &nb);
         if (!st.good()) return st;
-        const int g5 = std::min(ny_, std::max(1, nb) * nsm_);
+        const int g5 = std::min(B_ * ny_, std::max(1, nb) * nsm_);
         CUtensorMap mc, ml;
         if (!(st = make_tmap(&mc, twc)).good()) return st;
         if (!(st = make_tmap(&ml, twl)).good()) return st;
@@ -1595,19 +1625,35 @@ class EngineT : public Engine {
     }
 
     Status autotune(double *stage_ms) override {
-        // save f^n; candidates run stages on the current state
-        double *save = reinterpret_cast<double *>(scratch_d_);   // >= 33 N doubles = 33 N reals of either width
-        FFTLB_CU(cudaMemcpyAsync(save, f0_, Q * N_ * sizeof(real), cudaMemcpyDeviceToDevice, stream_));
-        cudaEvent_t e0, e1;
-        FFTLB_CU(cudaEventCreate(&e0));
-        FFTLB_CU(cudaEventCreate(&e1));
+        // candidates time stages on the current state of every run, writing
+        // to the RK stage buffer (or, for Euler, to a temporary one), so the
+        // state itself is never changed
+        real *out = f1b_;
+        void *tmp = nullptr;
+        if (!out) {
+            if (cudaMalloc(&tmp, (size_t)B_ * Q * N_ * sizeof(real)) != cudaSuccess) {
+                cudaGetLastError();
+                return Status::err(FFTLB_ERR_OOM, "autotune: no room for a stage output buffer");
+            }
+            out = reinterpret_cast<real *>(tmp);
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        auto cleanup = [&]() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (tmp) cudaFree(tmp);
+        };
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            cleanup();
+            return Status::err(FFTLB_ERR_CUDA, "autotune: event creation failed");
+        }
         auto time_stage = [&](double *ms) -> Status {
             Status st;
             for (int w = 0; w < 2; ++w)
-                if (!(st = stage(f0_, nullptr, f1_ ? f1_ : f0_, real(0), real(1))).good()) return st;
+                if (!(st = stage(f0b_, nullptr, out, real(0), real(1))).good()) return st;
             FFTLB_CU(cudaEventRecord(e0, stream_));
             for (int w = 0; w < 3; ++w)
-                if (!(st = stage(f0_, nullptr, f1_ ? f1_ : f0_, real(0), real(1))).good()) return st;
+                if (!(st = stage(f0b_, nullptr, out, real(0), real(1))).good()) return st;
             FFTLB_CU(cudaEventRecord(e1, stream_));
             FFTLB_CU(cudaEventSynchronize(e1));
             float t = 0;
@@ -1637,11 +1683,10 @@ class EngineT : public Engine {
             Status s2 = set_tuning(best);
             if (st.good() && !s2.good()) st = s2;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        if (st.good() && cudaStreamSynchronize(stream_) != cudaSuccess)
+            st = Status::err(FFTLB_ERR_CUDA, "autotune: stream synchronisation failed");
+        cleanup();
         if (!st.good()) return st;
-        FFTLB_CU(cudaMemcpyAsync(f0_, save, Q * N_ * sizeof(real), cudaMemcpyDeviceToDevice, stream_));
-        FFTLB_CU(cudaStreamSynchronize(stream_));
         if (stage_ms) *stage_ms = best_ms;
         return Status::ok();
     }
@@ -1649,12 +1694,12 @@ class EngineT : public Engine {
   private:
     Status launch_col(int first, int count, bool level1) {
         if (level1)
-            kcol_pipe<real, true><<<gridl_, NTC, smeml_, stream_>>>(spec_, groups_ + first, count, kxt_,
+            kcol_pipe<real, true><<<gridl_, NTC, smeml_, stream_>>>(specb_, groups_ + first, count, kxt_,
                                                                                kyt_, Wc_, Tc_, ntc_, kp_, TWl_, BOXR_,
                                                                                tmap_l1_, err_);
         else
             kcol_pipe<real, false><<<gridc_, NTC, smemc_, stream_>>>(
-                spec_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
+                specb_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
         FFTLB_LAUNCHED("kcol_pipe");
         return Status::ok();
     }
@@ -1663,15 +1708,15 @@ class EngineT : public Engine {
         Status st;
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
         if (SMAX1_ == 1)
-            k1_pipe<real, 1><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 1><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 2)
-            k1_pipe<real, 2><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 2><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 4)
-            k1_pipe<real, 4><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
+            k1_pipe<real, 4><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
         else
-            k1_pipe<real, 8><<<grid1_, NT1, smem1_, stream_>>>(cur, spec_, fields_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
+            k1_pipe<real, 8><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
         FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
@@ -1681,7 +1726,7 @@ class EngineT : public Engine {
         if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
-        k3_pipe<real><<<ny_, NT3, smem3_, stream_>>>(spec_, fields_, aux_, Wr_, Wp_, Tr_, ntr_, kp_, WR3_, err_);
+        k3_pipe<real><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, Tr_, ntr_, kp_, WR3_, err_);
         FFTLB_LAUNCHED("k3_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL2)).good()) return st;
@@ -1689,13 +1734,13 @@ class EngineT : public Engine {
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         if (SMAX5_ == 1)
-            k5_pipe<real, 1><<<grid5_, NT5, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 1><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         else if (SMAX5_ == 2)
-            k5_pipe<real, 2><<<grid5_, NT5, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 2><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         else
-            k5_pipe<real, 4><<<grid5_, NT5, smem5_, stream_>>>(spec_, fields_, aux_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 4><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
         FFTLB_LAUNCHED("k5_pipe");
         return prof_end();

@@ -119,14 +119,16 @@ __device__ void rows_fft_to_A(C *A, Lay la, C *wk, Lay lb, int n, int nrows, int
 
 template <typename real>
 __device__ __forceinline__ void k1_issue(const real *f, real *dst, uint64_t *bar, int j, int nchunk, int CH, int nx,
-                                         size_t N) {
+                                         int ny, size_t N) {
     const int ri = j / nchunk, c = j - ri * nchunk;
-    const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int yg = (int)blockIdx.x + ri * (int)gridDim.x;   // row over all runs
+    const int run = yg / ny, y = yg - run * ny;
     const int i0 = c * CH, nf = min(CH, Q - i0);
     const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
+    const real *fr = f + (size_t)run * Q * N;
     mbar_expect_tx(bar, (uint32_t)nf * rowbytes);
     for (int r = 0; r < nf; ++r)
-        bulk_g2s(dst + (size_t)r * nx, f + (size_t)(i0 + r) * N + (size_t)y * nx, rowbytes, bar);
+        bulk_g2s(dst + (size_t)r * nx, fr + (size_t)(i0 + r) * N + (size_t)y * nx, rowbytes, bar);
 }
 
 template <typename real, int SMAX>
@@ -153,7 +155,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
     C *wk = (C *)sc.take((size_t)CH * ph * sizeof(C));
     const Lay la{h, 1, 0}, lb{ph, 1, 1};
     const int nchunk = (Q + CH - 1) / CH;
-    const int nrows = (int)blockIdx.x < ny ? (ny - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int NY = P.nrun * ny;   // rows of all runs
+    const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int njobs = nrows * nchunk;
     if (tid == 0) {
         mbar_init(&bar0, 1);
@@ -165,8 +168,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
     load_tab(Tr, Tr_g, ntr, NT);
     __syncthreads();
     if (tid == 0) {
-        if (njobs > 0) k1_issue(f, buf0, &bar0, 0, nchunk, CH, nx, N);
-        if (njobs > 1) k1_issue(f, buf1, &bar1, 1, nchunk, CH, nx, N);
+        if (njobs > 0) k1_issue(f, buf0, &bar0, 0, nchunk, CH, nx, ny, N);
+        if (njobs > 1) k1_issue(f, buf1, &bar1, 1, nchunk, CH, nx, ny, N);
     }
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1;
@@ -177,7 +180,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
         const bool odd = j & 1;
         uint64_t *bar = odd ? &bar1 : &bar0;
         const int ri = j / nchunk, c = j - ri * nchunk;
-        const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int run = yg / ny, y = yg - run * ny;
+        C *spec_r = spec + (size_t)run * NSLOT * slot;
+        real *fields_r = fields + (size_t)run * 4 * N;
         const int i0 = c * CH, nf = min(CH, Q - i0);
         if (!block_wait(bar, odd ? par1 : par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
             r2c_post_l(res, lr, h, nf - r0, Wp, tid, NT);
             __syncthreads();
             for (int r = r0; r < nf; ++r) {
-                C *dst = spec + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
+                C *dst = spec_r + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
                 for (int k = tid; k < h; k += NT) dst[k] = res[lr(r - r0, k)];
             }
         }
@@ -231,10 +237,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
                     const real rho = a0[s], ux = a1[s] / rho, uy = a2[s] / rho;
                     const real T = real(0.5) * (a3[s] / rho - (ux * ux + uy * uy));
                     const size_t o = (size_t)y * nx + x;
-                    fields[o] = rho;
-                    fields[N + o] = ux;
-                    fields[2 * N + o] = uy;
-                    fields[3 * N + o] = T;
+                    fields_r[o] = rho;
+                    fields_r[N + o] = ux;
+                    fields_r[2 * N + o] = uy;
+                    fields_r[3 * N + o] = T;
                     B[x] = rho;
                     B[nx + x] = ux;
                     B[2 * nx + x] = uy;
@@ -251,14 +257,14 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
             r2c_post_l(res, lr, h, 6, Wp, tid, NT);
             __syncthreads();
             for (int r = 0; r < 6; ++r) {
-                C *dst = spec + (size_t)(SLOT_RHO + r) * slot + (size_t)y * h;
+                C *dst = spec_r + (size_t)(SLOT_RHO + r) * slot + (size_t)y * h;
                 for (int k = tid; k < h; k += NT) dst[k] = res[lr(r, k)];
             }
         }
         fence_proxy_async();
         __syncthreads();
         if (tid == 0 && j + 2 < njobs) {
-            k1_issue(f, B, bar, j + 2, nchunk, CH, nx, N);
+            k1_issue(f, B, bar, j + 2, nchunk, CH, nx, ny, N);
             if (odd) pend1 = true;
             else pend0 = true;
         }
@@ -340,17 +346,20 @@ __device__ __forceinline__ void col_multiply(typename cplx_of<real>::type *out, 
     }
 }
 
+// job -> (run, group, tile): jobs run over the tiles of one group, then the
+// groups of one run, then the runs
 template <typename C>
 __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDesc *groups, int k, int ntiles,
-                                           int TW, int ny, int BOXR, const CUtensorMap *tmap) {
+                                           int ngroups, int TW, int ny, int BOXR, const CUtensorMap *tmap) {
     const int job = (int)blockIdx.x + k * (int)gridDim.x;
-    const int g = job / ntiles, t = job - g * ntiles;
+    const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
+    const int g = jr / ntiles, t = jr - g * ntiles;
     const GroupDesc *G = groups + g;
     const int nin = G->nin;
     const int tile = TW * ny;
     mbar_expect_tx(bar, (uint32_t)(nin * tile * sizeof(C)));
     for (int s = 0; s < nin; ++s) {
-        const int sl = G->in_slot[s];
+        const int sl = run * NSLOT + G->in_slot[s];   // the tensor spans the arenas of all runs
         for (int r0 = 0; r0 < ny; r0 += BOXR)
             tma_load_2d(dst + (size_t)s * tile + (size_t)r0 * TW, tmap, 2 * t * TW, sl * ny + r0, bar);
     }
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
     C *wk1 = MULTI ? (C *)sc.take((size_t)ptile * sizeof(C)) : nullptr;
     const Lay lt{1, TW, 0}, lw{1, TW, 1};   // staged tile / padded work tile
     const int ntiles = h / TW;
-    const int njobs_total = ngroups * ntiles;
+    const int njobs_total = P.nrun * ngroups * ntiles;
     const int njobs = (int)blockIdx.x < njobs_total ? (njobs_total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (tid == 0) {
         mbar_init(&bar0, 1);
@@ -402,8 +411,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
     load_tab(kys, kyt, ny, NT);
     __syncthreads();
     if (tid == 0) {
-        if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, TW, ny, BOXR, &tmap);
-        if (njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, TW, ny, BOXR, &tmap);
+        if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, ny, BOXR, &tmap);
+        if (njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, ny, BOXR, &tmap);
     }
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1;
@@ -412,8 +421,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
         const bool odd = k & 1;
         uint64_t *bar = odd ? &bar1 : &bar0;
         const int job = (int)blockIdx.x + k * (int)gridDim.x;
-        const int g = job / ntiles, t = job - g * ntiles;
+        const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
+        const int g = jr / ntiles, t = jr - g * ntiles;
         const int kx0 = t * TW;
+        C *spec_r = spec + (size_t)run * NSLOT * slot;
         if (tid == 0) gd = groups[g];
         if (!block_wait(bar, odd ? par1 : par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
@@ -441,7 +452,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                               : pp_fft_any<+1, true, 0, 1>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT);
             const C *R = w2 ? Y : X;
             const Lay lr = w2 ? ly : lx;
-            gout = spec + (size_t)gd.out_slot[0] * slot + kx0;
+            gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0;
             for (int idx = tid; idx < tile; idx += NT) {
                 const int e = idx >> lgTW, c = idx & (TW - 1);
                 gout[(size_t)e * h + c] = R[lr(c, e)];
@@ -473,7 +484,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                                   : pp_fft_any<+1, true, 0, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT);
                 const C *R = w2 ? F1 : F0;
                 const Lay lr = w2 ? lf1 : lf0;
-                gout = spec + (size_t)gd.out_slot[o] * slot + kx0;
+                gout = spec_r + (size_t)gd.out_slot[o] * slot + kx0;
                 for (int idx = tid; idx < tile; idx += NT) {
                     const int e = idx >> lgTW, c = idx & (TW - 1);
                     gout[(size_t)e * h + c] = R[lr(c, e)];
@@ -484,7 +495,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
         fence_proxy_async();
         __syncthreads();
         if (tid == 0 && k + 2 < njobs) {
-            kcol_issue(in0, bar, groups, k + 2, ntiles, TW, ny, BOXR, &tmap);
+            kcol_issue(in0, bar, groups, k + 2, ntiles, ngroups, TW, ny, BOXR, &tmap);
             if (odd) pend1 = true;
             else pend0 = true;
         }
@@ -507,8 +518,12 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const int nx = P.nx, ny = P.ny, h = P.h, tid = threadIdx.x;
+    const int run = (int)blockIdx.x / ny, y = (int)blockIdx.x - run * ny;   // one row of one run per block
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    spec += (size_t)run * NSLOT * slot;
+    fields += (size_t)run * 4 * N;
+    aux += (size_t)run * 3 * N;
     const int ph = padded_len(h);
     SmemCursor sc{smem_raw, 0u};
     C *Wr = (C *)sc.take(h * sizeof(C));
@@ -597,9 +612,11 @@ constexpr int NHEAD = 10;   // dLx, dLy, dPhi spectra; rho, ux, uy, T; Cn, Bnx, 
 
 template <typename real>
 __device__ __forceinline__ void k5_issue_chunk(const typename cplx_of<real>::type *spec, real *dst, uint64_t *bar,
-                                               int j, int nchunk, int CH, int nx, size_t slot, int h) {
+                                               int j, int nchunk, int CH, int nx, int ny, size_t slot, int h) {
     const int ri = j / nchunk, c = j - ri * nchunk;
-    const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int run = yg / ny, y = yg - run * ny;
+    spec += (size_t)run * NSLOT * slot;
     const int v0 = c * CH, nv = min(CH, NMOV - v0);
     const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
     mbar_expect_tx(bar, (uint32_t)nv * rowbytes);
@@ -609,9 +626,13 @@ __device__ __forceinline__ void k5_issue_chunk(const typename cplx_of<real>::typ
 
 template <typename real>
 __device__ __forceinline__ void k5_issue_head(const typename cplx_of<real>::type *spec, const real *fields,
-                                              const real *aux, real *dst, uint64_t *bar, int ri, int nx, size_t N,
-                                              size_t slot, int h) {
-    const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+                                              const real *aux, real *dst, uint64_t *bar, int ri, int nx, int ny,
+                                              size_t N, size_t slot, int h) {
+    const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int run = yg / ny, y = yg - run * ny;
+    spec += (size_t)run * NSLOT * slot;
+    fields += (size_t)run * 4 * N;
+    aux += (size_t)run * 3 * N;
     const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
     mbar_expect_tx(bar, (uint32_t)NHEAD * rowbytes);
     bulk_g2s(dst, spec + (size_t)(SLOT_L2 + 0) * slot + (size_t)y * h, rowbytes, bar);
@@ -652,7 +673,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
     C *wk = (C *)sc.take((size_t)max(CH, 3) * ph * sizeof(C));
     const Lay la{h, 1, 0}, lb{ph, 1, 1};
     const int nchunk = (NMOV + CH - 1) / CH;
-    const int nrows = (int)blockIdx.x < ny ? (ny - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int NY = P.nrun * ny;   // rows of all runs
+    const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int njobs = nrows * nchunk;
     if (tid == 0) {
         mbar_init(&bar0, 1);
@@ -666,10 +688,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
     load_tab(Tr, Tr_g, ntr, NT);
     __syncthreads();
     if (tid == 0) {
-        if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, N, slot, h);
-        if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, N, slot, h);
-        if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, nchunk, CH, nx, slot, h);
-        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, nchunk, CH, nx, slot, h);
+        if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, h);
+        if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, h);
+        if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, nchunk, CH, nx, ny, slot, h);
+        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, nchunk, CH, nx, ny, slot, h);
     }
     uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
@@ -679,7 +701,9 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         const bool odd = j & 1;
         const int ri = j / nchunk, c = j - ri * nchunk;
         const bool hodd = (NHB > 1) && (ri & 1);
-        const int y = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int run = yg / ny, y = yg - run * ny;
+        const size_t fo = (size_t)run * Q * N;   // this run's distributions
         const int v0 = c * CH, nv = min(CH, NMOV - v0);
         real *H = hodd ? head1 : head0;
         if (c == 0) {
@@ -730,7 +754,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
                     weights_Fk<real>(T, F);
                     const real qq = real(0.5) * u2 / T, om = real(1) - qq;
                     const real fe = rho * F[0] * (om + real(0.5) * qq * qq);
-                    const size_t o = (size_t)y * nx + x;
+                    const size_t o = fo + (size_t)y * nx + x;
                     const real fc = fcur[o];
                     real fn = beta * (fc + dt * (-(fc - fe) * itau - e0 * fe));
                     if (with_base) fn += alpha * fbase[o];
@@ -765,7 +789,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
             const int x = tid + s * NT;
             if (x >= nx) continue;
             real fc[CHMAX5], fb[CHMAX5];
-            const size_t o0 = (size_t)(1 + v0) * N + (size_t)y * nx + x;
+            const size_t o0 = fo + (size_t)(1 + v0) * N + (size_t)y * nx + x;
             const real *pc = fcur + o0;
             const real *pb = fbase + o0;
 #pragma unroll
@@ -809,14 +833,14 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         __syncthreads();
         if (tid == 0) {
             if (j + 2 < njobs) {
-                k5_issue_chunk<real>(spec, B, odd ? &bar1 : &bar0, j + 2, nchunk, CH, nx, slot, h);
+                k5_issue_chunk<real>(spec, B, odd ? &bar1 : &bar0, j + 2, nchunk, CH, nx, ny, slot, h);
                 if (odd) pend1 = true;
                 else pend0 = true;
             }
             // the row's head buffer is free after its last chunk: prefetch
             // the head of row ri + NHB into it
             if (c == nchunk - 1 && ri + NHB < nrows) {
-                k5_issue_head<real>(spec, fields, aux, H, hodd ? &hbar1 : &hbar0, ri + NHB, nx, N, slot, h);
+                k5_issue_head<real>(spec, fields, aux, H, hodd ? &hbar1 : &hbar0, ri + NHB, nx, ny, N, slot, h);
                 if (hodd) hpend1 = true;
                 else hpend0 = true;
             }
