@@ -245,8 +245,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 companion measurement")
     ap.add_argument("--ncu-traffic-from", default=None, metavar="CSV",
                     help="write profiles/ncu_traffic.txt from an ncu --csv log of one step (no GPU work)")
-    ap.add_argument("--sweep", action="store_true",
-                    help="also time the batched sweep (64 runs of uneven grids replayed as one CUDA graph)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the batched sweep (64 runs of uneven grids, one persistent launch per kernel per "
+                         "parameter group, replayed as one CUDA graph)")
     args = ap.parse_args()
     if args.ncu_traffic_from:
         res = write_ncu_traffic(args.ncu_traffic_from, args.precision, args.grid,
@@ -373,7 +374,7 @@ def main():
                "d2h_bytes_per_step": 48 + fb / K}
 
     sweep = None
-    if args.sweep:
+    if not args.no_sweep:
         # batched phase-diagram sweep: 64 spinodal quenches (rho_c, T_r T_c) of
         # uneven grids, one CUDA graph per step
         plan = workloads.sweep_plan(64, seed=3)
