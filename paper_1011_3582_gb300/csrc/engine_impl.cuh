@@ -1500,18 +1500,25 @@ class EngineT : public Engine {
         if (!(st = pick_tw(true, &TWl_, &smeml_, &gridl_)).good()) return st;
         if (!(st = make_tmap(&tmap_conv_, TWc_)).good()) return st;
         if (!(st = make_tmap(&tmap_l1_, TWl_)).good()) return st;
-        // K3
-        WR3_ = 0;
-        for (int wr = ND1; wr >= 1; --wr) {
-            smem3_ = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs,
-                                 (size_t)2 * nx_ * rs});
-            if (smem3_ <= budget) {
-                WR3_ = wr;
-                break;
+        // K3 (one row per block, not pipelined inside a block): most blocks
+        // per SM first, so that one block's row loads overlap another's
+        // transforms, then the most work rows
+        {
+            int bestnb = 0;
+            WR3_ = 0;
+            for (int wr = ND1; wr >= 1; --wr) {
+                const size_t sm = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs,
+                                              (size_t)2 * nx_ * rs});
+                if (sm > budget) continue;
+                if (!(st = occupancy(k3_pipe<real>, NT3, sm, &nb)).good()) return st;
+                if (nb > bestnb) {
+                    bestnb = nb;
+                    WR3_ = wr;
+                    smem3_ = sm;
+                }
             }
         }
         if (!WR3_) return Status::err(FFTLB_ERR_ARG, "grid too large for the level-1 row kernel");
-        if (!(st = occupancy(k3_pipe<real>, NT3, smem3_, &nb)).good()) return st;
         // K5: most blocks per SM first, then two head buffers, then the
         // largest chunk
         {

@@ -352,6 +352,185 @@ __device__ int pp_fft_p2(C *A, int abs_, int aes, C *B, int bbs, int bes, int n,
     return where;
 }
 
+// ---------------------------------------------------------------------------
+// Forward transform, spectral multiply and inverse transform of power-of-two
+// columns with one pass fused.  With the forward transform written as the
+// passes F = P_L ... P_1 (pp_pass_p2, P_1 first), the inverse up to the
+// factor n is the adjoint F^H = P_1^H ... P_L^H.  The adjoint of a pass reads
+// where the pass writes, applies the opposite-direction R-point DFT,
+// multiplies by the conjugate twiddles and writes where the pass reads.  P_L,
+// the diagonal multiply and P_L^H touch only the R elements one butterfly
+// owns, so they run in registers, in place: L - 1 + 1 + L - 1 passes
+// through shared memory instead of 2 L + 1.
+// ---------------------------------------------------------------------------
+
+// the schedule of pp_fft_p2 for n = 2^logn: radix of pass p and the offset
+// of its twiddle table
+__device__ __forceinline__ void p2_schedule(int logn, int p, int *lr, int *logNs, int *toff) {
+    int lns = 0, rem = logn, off = 0;
+    for (int q = 0; q < p; ++q) {
+        const int l = rem >= 4 ? 4 : rem;
+        if (lns > 0) off += 1 << (lns + l);
+        lns += l;
+        rem -= l;
+    }
+    *lr = rem >= 4 ? 4 : rem;
+    *logNs = lns;
+    *toff = off;
+}
+
+__device__ __forceinline__ int p2_npasses(int logn) { return (logn + 3) / 4; }
+
+// adjoint of pp_pass_p2<R, -1, BFAST> (src read at its write positions, dst
+// written at its read positions)
+template <int R, bool BFAST, int PADS, int PADD, typename C>
+__device__ __forceinline__ void pp_pass_p2_adj(const C *src, int sbs, int ses, C *dst, int dbs, int des, int logn,
+                                               int nbatch, int lognbatch, int logNs, const C *T, int tid, int nthr) {
+    constexpr int LR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    const int lognb = logn - LR;
+    const int nb = 1 << lognb;
+    const int Ns = 1 << logNs;
+    const int total = nbatch << lognb;
+    for (int J = tid; J < total; J += nthr) {
+        int b, jj;
+        if (BFAST) {
+            b = J & (nbatch - 1);
+            jj = J >> lognbatch;
+        } else {
+            b = J >> lognb;
+            jj = J & (nb - 1);
+        }
+        const int k = jj & (Ns - 1);
+        const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
+        C v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = idxD + t * Ns;
+            v[t] = src[b * sbs + (PADS ? e + (e >> 4) : e) * ses];
+        }
+        SmallDFT<R, +1, C>::run(v);
+        if (Ns > 1) {
+            const C *tw = T + k;
+#pragma unroll
+            for (int t = 1; t < R; ++t) v[t] = cmul(v[t], cconj(tw[t * Ns]));
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = jj + t * nb;
+            dst[b * dbs + (PADD ? e + (e >> 4) : e) * des] = v[t];
+        }
+    }
+}
+
+template <bool BFAST, int PADS, int PADD, typename C>
+__device__ __forceinline__ void pp_pass_p2_adj_r(int lr, const C *src, int sbs, int ses, C *dst, int dbs, int des,
+                                                 int logn, int nbatch, int lognbatch, int logNs, const C *T, int tid,
+                                                 int nthr) {
+    if (lr == 4) pp_pass_p2_adj<16, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+    else if (lr == 3) pp_pass_p2_adj<8, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+    else if (lr == 2) pp_pass_p2_adj<4, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+    else pp_pass_p2_adj<2, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+}
+
+template <bool BFAST, int PADS, int PADD, typename C>
+__device__ __forceinline__ void pp_pass_p2_fwd_r(int lr, const C *src, int sbs, int ses, C *dst, int dbs, int des,
+                                                 int logn, int nbatch, int lognbatch, int logNs, const C *T, int tid,
+                                                 int nthr) {
+    if (lr == 4) pp_pass_p2<16, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+    else if (lr == 3) pp_pass_p2<8, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+    else if (lr == 2) pp_pass_p2<4, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+    else pp_pass_p2<2, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
+}
+
+// the fused last pass: forward pass L (read at its read positions), multiply
+// output element e of transform b by mult(b, e), adjoint of pass L, write
+// back to the same positions, times scale
+template <int R, bool BFAST, int PAD, typename C, typename Mult>
+__device__ __forceinline__ void pp_pass_p2_fused(C *buf, int bs, int es, int logn, int nbatch, int lognbatch,
+                                                 int logNs, const C *T, const Mult &mult, int tid, int nthr) {
+    using real = decltype(buf[0].x);
+    constexpr int LR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    const int lognb = logn - LR;
+    const int nb = 1 << lognb;
+    const int Ns = 1 << logNs;
+    const int total = nbatch << lognb;
+    for (int J = tid; J < total; J += nthr) {
+        int b, jj;
+        if (BFAST) {
+            b = J & (nbatch - 1);
+            jj = J >> lognbatch;
+        } else {
+            b = J >> lognb;
+            jj = J & (nb - 1);
+        }
+        const int k = jj & (Ns - 1);
+        const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
+        C v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = jj + t * nb;
+            v[t] = buf[b * bs + (PAD ? e + (e >> 4) : e) * es];
+        }
+        const C *tw = T + k;
+        if (Ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) v[t] = cmul(v[t], tw[t * Ns]);
+        }
+        SmallDFT<R, -1, C>::run(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = mult(b, idxD + t * Ns, v[t]);
+        SmallDFT<R, +1, C>::run(v);
+        if (Ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) v[t] = cmul(v[t], cconj(tw[t * Ns]));
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = jj + t * nb;
+            buf[b * bs + (PAD ? e + (e >> 4) : e) * es] = v[t];
+        }
+    }
+    (void)sizeof(real);
+}
+
+// y = F^H diag(mult) F x for nbatch power-of-two transforms of length n:
+// A (layout la, unpadded) holds x; B (layout lb, padded) is the work buffer.
+// Returns 0 if y is in A, 1 if in B.  Every pass ends with a block barrier;
+// callers synchronise before.
+template <bool BFAST, typename C, typename Mult>
+__device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *T, const Mult &mult, int tid,
+                          int nthr) {
+    const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
+    int where = 0, lr, lns, toff;
+    for (int p = 0; p < L - 1; ++p) {   // forward passes 1 .. L-1
+        p2_schedule(logn, p, &lr, &lns, &toff);
+        if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        __syncthreads();
+        where ^= 1;
+    }
+    p2_schedule(logn, L - 1, &lr, &lns, &toff);
+    C *buf = where ? B : A;
+    const Lay lbuf = where ? lb : la;
+#define FFTLB_FUSED(RR)                                                                                         \
+    (lbuf.pad ? pp_pass_p2_fused<RR, BFAST, 1>(buf, lbuf.bs, lbuf.es, logn, nbatch, lognbatch, lns, T + toff, mult, tid, nthr) \
+              : pp_pass_p2_fused<RR, BFAST, 0>(buf, lbuf.bs, lbuf.es, logn, nbatch, lognbatch, lns, T + toff, mult, tid, nthr))
+    if (lr == 4) FFTLB_FUSED(16);
+    else if (lr == 3) FFTLB_FUSED(8);
+    else if (lr == 2) FFTLB_FUSED(4);
+    else FFTLB_FUSED(2);
+#undef FFTLB_FUSED
+    __syncthreads();
+    for (int p = L - 2; p >= 0; --p) {   // adjoint passes L-1 .. 1
+        p2_schedule(logn, p, &lr, &lns, &toff);
+        if (where == 0) pp_pass_p2_adj_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        else pp_pass_p2_adj_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        __syncthreads();
+        where ^= 1;
+    }
+    return where;
+}
+
 // Dispatch: the shift-based passes when n (and, for BFAST, nbatch) is a
 // power of two, the generic passes otherwise.  PADA / PADB must match
 // la.pad / lb.pad.

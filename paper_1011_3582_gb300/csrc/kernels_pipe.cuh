@@ -348,6 +348,19 @@ __device__ __forceinline__ void col_multiply(typename cplx_of<real>::type *out, 
 
 // job -> (run, group, tile): jobs run over the tiles of one group, then the
 // groups of one run, then the runs
+// the convection multiplier i (v_x k_x + v_y k_y) (general form of
+// col_multiply's terms) times the inverse normalisation, for the fused pass
+// of pp_conv_p2: b = column within the tile, e = k_y bin
+template <typename real> struct ColMult {
+    using C = typename cplx_of<real>::type;
+    real c0, c1, c2, c3, c4, scale;
+    const real *kxs, *kys;
+    int kx0;
+    __device__ __forceinline__ C operator()(int b, int e, C v) const {
+        return cscale(mult_apply<real>(c0, c1, c2, c3, c4, kxs[kx0 + b], kys[e], v), scale);
+    }
+};
+
 template <typename C>
 __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDesc *groups, int k, int ntiles,
                                            int ngroups, int TW, int ny, int BOXR, const CUtensorMap *tmap) {
@@ -387,6 +400,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
     const int tile = TW * ny;
     const int ptile = TW * padded_len(ny);
     const int lgTW = ilog2(TW);   // TW is a power of two
+    const bool pow2ny = is_pow2(ny);
     SmemCursor sc{smem_raw, 0u};
     C *Wc = (C *)sc.take(ny * sizeof(C));
     C *Tc = (C *)sc.take(ntc * sizeof(C));
@@ -441,17 +455,31 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
         C *in0 = odd ? buf1 : buf0;
         C *gout;
         if (!MULTI) {
-            // convection: forward, multiply in place, inverse, store
-            const int w1 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
-            C *X = w1 ? wk0 : in0;
-            C *Y = w1 ? in0 : wk0;
-            const Lay lx = w1 ? lw : lt, ly = w1 ? lt : lw;
-            col_multiply<real>(X, lx, X, lx, X, lx, gd, 0, kxs, kys, kx0, TW, lgTW, ny, h, scale, NT);
-            __syncthreads();
-            const int w2 = w1 ? pp_fft_any<+1, true, 1, 0>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT)
-                              : pp_fft_any<+1, true, 0, 1>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT);
-            const C *R = w2 ? Y : X;
-            const Lay lr = w2 ? ly : lx;
+            const C *R;
+            Lay lr;
+            if (pow2ny && kx0 != 0) {
+                // convection, power-of-two columns: forward passes, the last
+                // pass fused with the multiply and its adjoint, adjoint passes
+                const ColMult<real> m{(real)gd.c[0][0][0], (real)gd.c[0][0][1], (real)gd.c[0][0][2],
+                                      (real)gd.c[0][0][3], (real)gd.c[0][0][4], scale, kxs, kys, kx0};
+                const int w = pp_conv_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, m, tid, NT);
+                R = w ? wk0 : in0;
+                lr = w ? lw : lt;
+            } else {
+                // convection (the tile holding k_x = 0 pairs (k_y, -k_y) of the
+                // packed DC / row-Nyquist column; other lengths): forward,
+                // multiply in place, inverse
+                const int w1 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
+                C *X = w1 ? wk0 : in0;
+                C *Y = w1 ? in0 : wk0;
+                const Lay lx = w1 ? lw : lt, ly = w1 ? lt : lw;
+                col_multiply<real>(X, lx, X, lx, X, lx, gd, 0, kxs, kys, kx0, TW, lgTW, ny, h, scale, NT);
+                __syncthreads();
+                const int w2 = w1 ? pp_fft_any<+1, true, 1, 0>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT)
+                                  : pp_fft_any<+1, true, 0, 1>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT);
+                R = w2 ? Y : X;
+                lr = w2 ? ly : lx;
+            }
             gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0;
             for (int idx = tid; idx < tile; idx += NT) {
                 const int e = idx >> lgTW, c = idx & (TW - 1);
