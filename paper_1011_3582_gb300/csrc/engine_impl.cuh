@@ -905,8 +905,9 @@ class EngineT : public Engine {
     C *spec_ = nullptr;
     real *kxt_ = nullptr, *kyt_ = nullptr;
     C *Wr_ = nullptr, *Wp_ = nullptr, *Wc_ = nullptr;
-    C *Tr_ = nullptr, *Tc_ = nullptr;   // pass twiddle tables (power-of-two lengths)
-    int ntr_ = 0, ntc_ = 0;
+    C *Tr_ = nullptr, *Tc_ = nullptr;   // pass twiddle tables (power-of-two lengths), radix 16 first
+    C *Tr8_ = nullptr;                  // rows, radix 8 first
+    int ntr_ = 0, ntc_ = 0, ntr8_ = 0;
     GroupDesc *groups_ = nullptr;
     double *partial_ = nullptr, *red_ = nullptr;
     void *scratch_d_ = nullptr;
@@ -1152,7 +1153,7 @@ class EngineT : public Engine {
 
     // per-pass twiddle tables of the power-of-two passes (see
     // pass_twiddle_len): T[t Ns + k] = exp(-2 pi i t k / (Ns R))
-    static void pass_twiddles(std::vector<C> &T, int n) {
+    static void pass_twiddles(std::vector<C> &T, int n, int maxlr) {
         T.clear();
         if (!is_pow2(n)) return;
         const long double pi = 3.141592653589793238462643383279502884L;
@@ -1160,7 +1161,7 @@ class EngineT : public Engine {
         while ((1 << logn) < n) ++logn;
         int logNs = 0, rem = logn;
         while (rem > 0) {
-            const int lr = rem >= 4 ? 4 : rem;
+            const int lr = rem >= maxlr ? maxlr : rem;
             if (logNs > 0) {
                 const int Ns = 1 << logNs, R = 1 << lr;
                 for (int t = 0; t < R; ++t)
@@ -1190,15 +1191,19 @@ class EngineT : public Engine {
         FFTLB_CU(cudaMemcpy(Wr_, wr.data(), wr.size() * sizeof(C), cudaMemcpyHostToDevice));
         FFTLB_CU(cudaMemcpy(Wp_, wp.data(), wp.size() * sizeof(C), cudaMemcpyHostToDevice));
         FFTLB_CU(cudaMemcpy(Wc_, wc.data(), wc.size() * sizeof(C), cudaMemcpyHostToDevice));
-        std::vector<C> tr, tc;
-        pass_twiddles(tr, h_);
-        pass_twiddles(tc, ny_);
+        std::vector<C> tr, tr8, tc;
+        pass_twiddles(tr, h_, 4);
+        pass_twiddles(tr8, h_, 3);
+        pass_twiddles(tc, ny_, 4);
         ntr_ = (int)tr.size();
+        ntr8_ = (int)tr8.size();
         ntc_ = (int)tc.size();
         Status st;
         if (!(st = dalloc(&Tr_, std::max<size_t>(1, tr.size()))).good()) return st;
+        if (!(st = dalloc(&Tr8_, std::max<size_t>(1, tr8.size()))).good()) return st;
         if (!(st = dalloc(&Tc_, std::max<size_t>(1, tc.size()))).good()) return st;
         if (ntr_) FFTLB_CU(cudaMemcpy(Tr_, tr.data(), tr.size() * sizeof(C), cudaMemcpyHostToDevice));
+        if (ntr8_) FFTLB_CU(cudaMemcpy(Tr8_, tr8.data(), tr8.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntc_) FFTLB_CU(cudaMemcpy(Tc_, tc.data(), tc.size() * sizeof(C), cudaMemcpyHostToDevice));
         return Status::ok();
     }
@@ -1402,6 +1407,10 @@ class EngineT : public Engine {
 
     size_t budget_ = 0;
     static constexpr int NT1 = KCfg<real, KS_K1>::NT, NTC = KCfg<real, KS_COL>::NT, NT5 = KCfg<real, KS_K5>::NT;
+    int ntrmax() const { return std::max(ntr_, ntr8_); }
+    // largest row radix for a kernel transforming `rows` rows at a time with
+    // nthr threads: radix 16 unless its passes would leave threads idle
+    int row_maxlr(int rows, int nthr) const { return rows * (h_ / 16) < nthr ? 3 : 4; }
     static int smax_for(int nx, int nt, int cap) {
         const int s = (nx + nt - 1) / nt;
         int r = 1;
@@ -1507,7 +1516,7 @@ class EngineT : public Engine {
             int bestnb = 0;
             WR3_ = 0;
             for (int wr = ND1; wr >= 1; --wr) {
-                const size_t sm = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs,
+                const size_t sm = smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs,
                                               (size_t)2 * nx_ * rs});
                 if (sm > budget) continue;
                 if (!(st = occupancy(k3_pipe<real>, NT3, sm, &nb)).good()) return st;
@@ -1528,7 +1537,7 @@ class EngineT : public Engine {
                 for (int ch = CHMAX5; ch >= 2; ch -= 2) {
                     const size_t head = (size_t)NHEAD * nx_ * rs;
                     const size_t sm =
-                        smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
+                        smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
                                     (size_t)ch * nx_ * rs, (size_t)std::max(ch, 3) * ph * cs});
                     if (sm > budget) continue;
                     st = occ_k5(sm, &nb);
@@ -1594,7 +1603,7 @@ class EngineT : public Engine {
         const size_t smc = smem_bytes({ny_ * cs, ntc_ * cs, kt, tc, tc, ptc});
         const size_t sml = smem_bytes({ny_ * cs, ntc_ * cs, kt, 2 * tl, 2 * tl, ptl, ptl});
         const size_t head = (size_t)NHEAD * nx_ * rs;
-        const size_t sm5 = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, head, nhb > 1 ? head : 0, (size_t)ch5 * nx_ * rs,
+        const size_t sm5 = smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, (size_t)ch5 * nx_ * rs,
                                        (size_t)ch5 * nx_ * rs, (size_t)std::max(ch5, 3) * ph * cs});
         if (sm1 > budget_ || smc > budget_ || sml > budget_ || sm5 > budget_)
             return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
@@ -1733,22 +1742,27 @@ class EngineT : public Engine {
         if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
-        k3_pipe<real><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, Tr_, ntr_, kp_, WR3_, err_);
+        {
+            const int ml = row_maxlr(WR3_, NT3);
+            k3_pipe<real><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, ml == 3 ? Tr8_ : Tr_,
+                                                              ml == 3 ? ntr8_ : ntr_, kp_, WR3_, ml, err_);
+        }
         FFTLB_LAUNCHED("k3_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL2)).good()) return st;
         if (!(st = launch_col(l2_groups_, 3, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
+        const int ml5 = row_maxlr(CH5_, NT5);
         if (SMAX5_ == 1)
             k5_pipe<real, 1><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
+                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, ml5, err_);
         else if (SMAX5_ == 2)
             k5_pipe<real, 2><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
+                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, ml5, err_);
         else
             k5_pipe<real, 4><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, Tr_, ntr_, kp_, CH5_, NHB5_, err_);
+                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, ml5, err_);
         FFTLB_LAUNCHED("k5_pipe");
         return prof_end();
     }

@@ -305,16 +305,16 @@ __device__ __forceinline__ void pp_pass_p2(const C *src, int sbs, int ses, C *ds
 }
 
 // Per-pass twiddle tables of a power-of-two length n for the radix plan of
-// pp_fft_p2 (16 while at least 4 bits remain, then 8 / 4 / 2): for every
-// pass with Ns > 1, Ns * R entries T[t Ns + k] = exp(-2 pi i t k / (Ns R))
-// (consecutive butterflies k read consecutive entries).
-// Total length pass_twiddle_len(n) <= 2 n.
-__host__ __device__ inline int pass_twiddle_len(int n) {
+// pp_fft_p2 with largest radix 2^maxlr (2^maxlr while at least maxlr bits
+// remain, then the rest): for every pass with Ns > 1, Ns * R entries
+// T[t Ns + k] = exp(-2 pi i t k / (Ns R)) (consecutive butterflies k read
+// consecutive entries).  Total length pass_twiddle_len(n) <= 2 n.
+__host__ __device__ inline int pass_twiddle_len(int n, int maxlr = 4) {
     int logn = 0;
     while ((1 << logn) < n) ++logn;
     int logNs = 0, rem = logn, len = 0;
     while (rem > 0) {
-        const int lr = rem >= 4 ? 4 : rem;
+        const int lr = rem >= maxlr ? maxlr : rem;
         if (logNs > 0) len += 1 << (logNs + lr);
         logNs += lr;
         rem -= lr;
@@ -324,14 +324,16 @@ __host__ __device__ inline int pass_twiddle_len(int n) {
 
 // pp_fft for power-of-two n with compile-time padding of A and B; T holds
 // the pass twiddle tables of n
+// the pass tables of n with largest radix 2^maxlr (4: radix 16; 3: radix 8,
+// for batches whose radix-16 passes would leave threads idle)
 template <int DIR, bool BFAST, int PADA, int PADB, typename C>
 __device__ int pp_fft_p2(C *A, int abs_, int aes, C *B, int bbs, int bes, int n, int nbatch, const C *T, int tid,
-                         int nthr) {
+                         int nthr, int maxlr = 4) {
     const int logn = ilog2(n), lognbatch = ilog2(nbatch);
     int logNs = 0, rem = logn, where = 0;
     const C *Tp = T;
     while (rem > 0) {
-        const int lr = rem >= 4 ? 4 : rem;   // radix 16, then 8 / 4 / 2 for the rest
+        const int lr = rem >= maxlr ? maxlr : rem;   // largest radix first, the rest last
         if (where == 0) {
             if (lr == 4) pp_pass_p2<16, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
             else if (lr == 3) pp_pass_p2<8, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
@@ -538,9 +540,9 @@ __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C
 // the shift-based ones, used when n is a power of two)
 template <int DIR, bool BFAST, int PADA, int PADB, typename C>
 __device__ __forceinline__ int pp_fft_any(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *W, const C *T,
-                                          int tid, int nthr) {
+                                          int tid, int nthr, int maxlr = 4) {
     if (is_pow2(n) && (!BFAST || is_pow2(nbatch)))
-        return pp_fft_p2<DIR, BFAST, PADA, PADB>(A, la.bs, la.es, B, lb.bs, lb.es, n, nbatch, T, tid, nthr);
+        return pp_fft_p2<DIR, BFAST, PADA, PADB>(A, la.bs, la.es, B, lb.bs, lb.es, n, nbatch, T, tid, nthr, maxlr);
     return pp_fft<DIR, BFAST>(A, la, B, lb, n, nbatch, W, tid, nthr);
 }
 

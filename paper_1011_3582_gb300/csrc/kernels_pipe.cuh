@@ -98,11 +98,11 @@ __device__ __forceinline__ real real_at(const typename cplx_of<real>::type *buf,
 // padded rows, a chunk at a time; results always end in A.
 template <int DIR, typename C>
 __device__ void rows_fft_to_A(C *A, Lay la, C *wk, Lay lb, int n, int nrows, int wrows, const C *W, const C *T,
-                              int nthr) {
+                              int nthr, int maxlr) {
     for (int r0 = 0; r0 < nrows; r0 += wrows) {
         const int nb = min(wrows, nrows - r0);
         C *a = A + (size_t)r0 * la.bs;
-        const int w = pp_fft_any<DIR, false, 0, 1>(a, la, wk, lb, n, nb, W, T, (int)threadIdx.x, nthr);
+        const int w = pp_fft_any<DIR, false, 0, 1>(a, la, wk, lb, n, nb, W, T, (int)threadIdx.x, nthr, maxlr);
         if (w) {
             for (int i = threadIdx.x; i < nb * n; i += nthr) {
                 const int r = i / n, e = i - r * n;
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
                                                const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                const typename cplx_of<real>::type *__restrict__ Tr_g, int ntr,
-                                               KP<real> P, int WR, int *err) {
+                                               KP<real> P, int WR, int maxlr, int *err) {
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     }
     c2r_pre_l(d, la, h, ND1, Wp, tid, NT3);
     __syncthreads();
-    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, Tr, NT3);
+    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, Tr, NT3, maxlr);
     const C *res = d;
     const Lay lr = la;
     real *dw = reinterpret_cast<real *>(d);
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
         dw[4 * nx + x] = q2 * Ty;
     }
     __syncthreads();
-    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, Tr, NT3);
+    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, Tr, NT3, maxlr);
     C *res2 = d;
     const Lay lr2 = la;
     r2c_post_l(res2, lr2, h, 5, Wp, tid, NT3);
@@ -682,7 +682,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
                                                              const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                              const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
-                                                             int ntr, KP<real> P, int CH, int NHB, int *err) {
+                                                             int ntr, KP<real> P, int CH, int NHB, int maxlr,
+                                                             int *err) {
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_K5>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
             C *l2 = reinterpret_cast<C *>(H);
             c2r_pre_l(l2, la, h, 3, Wp, tid, NT);
             __syncthreads();
-            const int w = pp_fft_any<+1, false, 0, 1>(l2, la, wk, lb, h, 3, Wr, Tr, tid, NT);
+            const int w = pp_fft_any<+1, false, 0, 1>(l2, la, wk, lb, h, 3, Wr, Tr, tid, NT, maxlr);
             const C *lres = w ? wk : l2;
             const Lay llr = w ? lb : la;
             // per-site coefficients, written over the head rows (same site,
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         C *Bc = reinterpret_cast<C *>(B);
         c2r_pre_l(Bc, la, h, nv, Wp, tid, NT);
         __syncthreads();
-        const int w = pp_fft_any<+1, false, 0, 1>(Bc, la, wk, lb, h, nv, Wr, Tr, tid, NT);
+        const int w = pp_fft_any<+1, false, 0, 1>(Bc, la, wk, lb, h, nv, Wr, Tr, tid, NT, maxlr);
         const C *cres = w ? wk : Bc;
         const Lay lcr = w ? lb : la;
 #pragma unroll 1
