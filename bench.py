@@ -245,6 +245,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 companion measurement")
     ap.add_argument("--ncu-traffic-from", default=None, metavar="CSV",
                     help="write profiles/ncu_traffic.txt from an ncu --csv log of one step (no GPU work)")
+    ap.add_argument("--no-cufft-reference", action="store_true",
+                    help="skip timing the PyTorch/cuFFT version of the same step")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the batched sweep (64 runs of uneven grids, one persistent launch per kernel per "
                          "parameter group, replayed as one CUDA graph)")
@@ -405,6 +407,31 @@ def main():
                  "graph_launches_per_step": 1, "create_and_autotune_s": t_create}
         bt.close()
 
+    cufft = None
+    if not args.no_cufft_reference:
+        # the same step written in PyTorch (torch.fft = cuFFT for the 94
+        # transforms, element-wise kernels for the rest), fp32, timed the
+        # same way: a reference for the hand-written kernels, not the product
+        from paper_1011_3582_gb300 import torch_reference as TR
+        ts = TR.TorchStep(n, n, a=A, b=B, integrator=3, window=4)
+        ts.set_fields(*fields)
+        ts.step(2)
+        kr = max(3, K // 10)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record()
+        ts.step(kr)
+        ev1.record()
+        torch.cuda.synchronize()
+        rms = maxed(ev0.elapsed_time(ev1))
+        cufft = {"value": world * n * n * kr / (rms * 1e-3) / 1e6, "unit": "MLUPS", "steps": kr,
+                 "ms_per_step": rms / kr, "dtype": "f32",
+                 "what": "same SSP-RK3 step in PyTorch: torch.fft (cuFFT) transforms + torch element-wise kernels"}
+        del ts
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
@@ -422,7 +449,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "kernels": kernels, "alg_bytes_per_step": step_bytes,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
-                "fp64": fp64, "sweep": sweep, "invariants_after": inv}
+                "fp64": fp64, "sweep": sweep, "cufft_reference": cufft, "invariants_after": inv}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -495,20 +495,30 @@ __device__ __forceinline__ void pp_pass_p2_fused(C *buf, int bs, int es, int log
     (void)sizeof(real);
 }
 
+// Barrier among the nthr threads that share a transform batch: the whole
+// block (id 0, __syncthreads) or a group of whole warps on a named barrier.
+struct GroupSync {
+    int id, nthr;
+    __device__ __forceinline__ void operator()() const {
+        if (id == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
+    }
+};
+
 // y = F^H diag(mult) F x for nbatch power-of-two transforms of length n:
 // A (layout la, unpadded) holds x; B (layout lb, padded) is the work buffer.
-// Returns 0 if y is in A, 1 if in B.  Every pass ends with a block barrier;
-// callers synchronise before.
+// Returns 0 if y is in A, 1 if in B.  Every pass ends with a barrier of the
+// nthr participating threads (sync); callers synchronise before.
 template <bool BFAST, typename C, typename Mult>
 __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *T, const Mult &mult, int tid,
-                          int nthr) {
+                          int nthr, const GroupSync &sync) {
     const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
     int where = 0, lr, lns, toff;
     for (int p = 0; p < L - 1; ++p) {   // forward passes 1 .. L-1
         p2_schedule(logn, p, &lr, &lns, &toff);
         if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
         else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
-        __syncthreads();
+        sync();
         where ^= 1;
     }
     p2_schedule(logn, L - 1, &lr, &lns, &toff);
@@ -522,12 +532,12 @@ __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C
     else if (lr == 2) FFTLB_FUSED(4);
     else FFTLB_FUSED(2);
 #undef FFTLB_FUSED
-    __syncthreads();
+    sync();
     for (int p = L - 2; p >= 0; --p) {   // adjoint passes L-1 .. 1
         p2_schedule(logn, p, &lr, &lns, &toff);
         if (where == 0) pp_pass_p2_adj_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
         else pp_pass_p2_adj_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
-        __syncthreads();
+        sync();
         where ^= 1;
     }
     return where;

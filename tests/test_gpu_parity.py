@@ -191,3 +191,19 @@ def test_spinodal_sweep_grids(fl, n, nsteps, precision):
         err = (np.abs(f_g - f_o) / np.abs(f_o)).max()
         print(f"fp32 {n}^2 after {nsteps} RK3 steps: max |df|/f = {err:.3e} (bound {bound:.3e})")
         assert err < bound
+
+
+def test_torch_cufft_reference_matches_oracle():
+    """The PyTorch/cuFFT step that bench.py times beside the CUDA kernels
+    computes the same method: fp32, same bound as the CUDA fp32 path."""
+    import torch
+    from paper_1011_3582_gb300 import torch_reference as TR
+    fields, kw, f_o = _spinodal_oracle(256, 3)
+    ts = TR.TorchStep(256, 256, a=A49, b=B21, integrator=3)
+    ts.set_fields(*fields)
+    ts.step(3)
+    f_t = ts.f.double().cpu().numpy()
+    bound = fp32_force_bound(256, 3, fields[0], fields[3])
+    err = (np.abs(f_t - f_o) / np.abs(f_o)).max()
+    print(f"torch/cuFFT fp32 256^2 after 3 RK3 steps: max |df|/f = {err:.3e} (bound {bound:.3e})")
+    assert err < bound
