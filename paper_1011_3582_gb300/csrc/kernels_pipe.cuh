@@ -457,27 +457,17 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
         if (!MULTI) {
             const C *R;
             Lay lr;
-            if (pow2ny && kx0 != 0 && TW >= 2 && NT % 64 == 0) {
+            if (pow2ny && kx0 != 0) {
                 // convection, power-of-two columns: forward passes, the last
-                // pass fused with the multiply and its adjoint, adjoint
-                // passes.  The two halves of the block each take half of the
-                // tile's columns and synchronise on their own named barrier,
-                // so that one half's barrier waits overlap the other's work.
-                const int half = tid / (NT / 2), htid = tid - half * (NT / 2), TWh = TW / 2;
+                // pass fused with the multiply and its adjoint, adjoint passes
+                // (splitting the tile's columns between two named-barrier
+                // halves measured slower: 228 -> 247 us at 1024^2, from the
+                // bank conflicts of half-width tiles)
                 const ColMult<real> m{(real)gd.c[0][0][0], (real)gd.c[0][0][1], (real)gd.c[0][0][2],
-                                      (real)gd.c[0][0][3], (real)gd.c[0][0][4], scale, kxs, kys, kx0 + half * TWh};
-                C *a = in0 + half * TWh, *bw = wk0 + half * TWh;
-                const int w = pp_conv_p2<true>(a, lt, bw, lw, ny, TWh, Tc, m, htid, NT / 2, GroupSync{1 + half, NT / 2});
-                const C *Rh = w ? bw : a;
-                const Lay lrh = w ? lw : lt;
-                gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0 + half * TWh;
-                const int lgTWh = lgTW - 1;
-                for (int idx = htid; idx < TWh * ny; idx += NT / 2) {
-                    const int e = idx >> lgTWh, c = idx & (TWh - 1);
-                    gout[(size_t)e * h + c] = Rh[lrh(c, e)];
-                }
-                R = nullptr;   // stored
-                lr = lt;
+                                      (real)gd.c[0][0][3], (real)gd.c[0][0][4], scale, kxs, kys, kx0};
+                const int w = pp_conv_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, m, tid, NT, GroupSync{0, NT});
+                R = w ? wk0 : in0;
+                lr = w ? lw : lt;
             } else {
                 // convection (the tile holding k_x = 0 pairs (k_y, -k_y) of the
                 // packed DC / row-Nyquist column; other lengths): forward,
@@ -493,12 +483,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 R = w2 ? Y : X;
                 lr = w2 ? ly : lx;
             }
-            if (R) {
-                gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0;
-                for (int idx = tid; idx < tile; idx += NT) {
-                    const int e = idx >> lgTW, c = idx & (TW - 1);
-                    gout[(size_t)e * h + c] = R[lr(c, e)];
-                }
+            gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0;
+            for (int idx = tid; idx < tile; idx += NT) {
+                const int e = idx >> lgTW, c = idx & (TW - 1);
+                gout[(size_t)e * h + c] = R[lr(c, e)];
             }
         } else {
             // X0 in {in0, wk0}, X1 in {in1, wk1}; outputs ping-pong between
