@@ -245,6 +245,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 companion measurement")
     ap.add_argument("--ncu-traffic-from", default=None, metavar="CSV",
                     help="write profiles/ncu_traffic.txt from an ncu --csv log of one step (no GPU work)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch parameters instead of fftlb_autotune's")
     ap.add_argument("--no-cufft-reference", action="store_true",
                     help="skip timing the PyTorch/cuFFT version of the same step")
     ap.add_argument("--no-sweep", action="store_true",
@@ -297,6 +299,9 @@ def main():
             clk.__enter__()
         h = fftlb.Handle(workload_params(fftlb, n, precision), stream=stream.cuda_stream)
         h.set_fields(*fields)
+        if not args.no_autotune:
+            h.autotune()   # launch parameters only; the state is untouched
+        tuned[precision] = h.tuning()
         busy0 = time.perf_counter()
         h.step(warmup)
         torch.cuda.synchronize()
@@ -325,6 +330,7 @@ def main():
         h.close()
         return ms, prof, inv, lps, (clk.summary(t0, t1, busy0, busy1) if sample_clocks else None)
 
+    tuned = {}
     ms, prof, inv, lps, clocks = time_path(args.precision, args.steps, args.warmup, True)
     K = args.steps
     value = world * n * n * K / (ms * 1e-3) / 1e6
@@ -360,6 +366,8 @@ def main():
         outs = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
         h = fftlb.Handle(workload_params(fftlb, n, args.precision), stream=stream.cuda_stream)
         h.set_fields(*pinned)
+        if not args.no_autotune:
+            h.tuning(tuned[args.precision])   # the parameters the timed run used
         h.step(2)
         torch.cuda.synchronize()
         barrier()
@@ -446,7 +454,10 @@ def main():
                            "tau": 1e-2, "K": 1e-5, "q": -0.004,
                            "l2": "inputs larger than L2 (state %.0f MB + spectra %.0f MB)" % (
                                33 * n * n * args.precision / 8 / 1e6, 58 * n * n * args.precision / 8 / 1e6),
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "launch_tuning": dict(zip(("tw_conv", "tw_level", "rows_forward", "rows_final",
+                                                      "head_buffers"), tuned[args.precision]),
+                                                 autotuned=not args.no_autotune)},
                 "roofline": roofline, "kernels": kernels, "alg_bytes_per_step": step_bytes,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
                 "fp64": fp64, "sweep": sweep, "cufft_reference": cufft, "invariants_after": inv}
