@@ -543,6 +543,124 @@ __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C
     return where;
 }
 
+// Several outputs from one or two inputs (the level-1 / level-2 derivative
+// groups): the inputs take the forward passes 1 .. L-1 once
+// (pp_fwd_head_p2); each output is then one fused pass, reading both inputs'
+// butterfly and applying their pass L, the per-element combination
+// mult(b, e, x0, x1) and the adjoint of pass L, written to a free buffer
+// (pp_pass_p2_fused2), and the adjoint passes L-1 .. 1 (pp_adj_tail_p2).
+
+template <bool BFAST, typename C>
+__device__ int pp_fwd_head_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *T, int tid, int nthr,
+                              const GroupSync &sync) {
+    const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
+    int where = 0, lr, lns, toff;
+    for (int p = 0; p < L - 1; ++p) {
+        p2_schedule(logn, p, &lr, &lns, &toff);
+        if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        sync();
+        where ^= 1;
+    }
+    return where;
+}
+
+template <int R, bool BFAST, int PADX, int PADQ, typename C, typename Mult2>
+__device__ __forceinline__ void pp_pass_p2_fused2(const C *X0, const C *X1, int xbs, int xes, bool two, C *Q, int qbs,
+                                                  int qes, int logn, int nbatch, int lognbatch, int logNs, const C *T,
+                                                  const Mult2 &mult, int tid, int nthr) {
+    constexpr int LR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    const int lognb = logn - LR;
+    const int nb = 1 << lognb;
+    const int Ns = 1 << logNs;
+    const int total = nbatch << lognb;
+    for (int J = tid; J < total; J += nthr) {
+        int b, jj;
+        if (BFAST) {
+            b = J & (nbatch - 1);
+            jj = J >> lognbatch;
+        } else {
+            b = J >> lognb;
+            jj = J & (nb - 1);
+        }
+        const int k = jj & (Ns - 1);
+        const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
+        const C *tw = T + k;
+        C v0[R], v1[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = jj + t * nb;
+            const int a = b * xbs + (PADX ? e + (e >> 4) : e) * xes;
+            v0[t] = X0[a];
+            v1[t] = two ? X1[a] : C{0, 0};
+        }
+        if (Ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                const C w = tw[t * Ns];
+                v0[t] = cmul(v0[t], w);
+                v1[t] = cmul(v1[t], w);
+            }
+        }
+        SmallDFT<R, -1, C>::run(v0);
+        if (two) SmallDFT<R, -1, C>::run(v1);
+#pragma unroll
+        for (int t = 0; t < R; ++t) v0[t] = mult(b, idxD + t * Ns, v0[t], v1[t]);
+        SmallDFT<R, +1, C>::run(v0);
+        if (Ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) v0[t] = cmul(v0[t], cconj(tw[t * Ns]));
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int e = jj + t * nb;
+            Q[b * qbs + (PADQ ? e + (e >> 4) : e) * qes] = v0[t];
+        }
+    }
+}
+
+// the fused output pass from inputs in layout lx to the buffer Q (layout lq)
+template <bool BFAST, typename C, typename Mult2>
+__device__ void pp_out_fused_p2(const C *X0, const C *X1, Lay lx, bool two, C *Q, Lay lq, int n, int nbatch,
+                                const C *T, const Mult2 &mult, int tid, int nthr, const GroupSync &sync) {
+    const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
+    int lr, lns, toff;
+    p2_schedule(logn, L - 1, &lr, &lns, &toff);
+#define FFTLB_F2(RR)                                                                                              \
+    if (lx.pad) {                                                                                                \
+        if (lq.pad) pp_pass_p2_fused2<RR, BFAST, 1, 1>(X0, X1, lx.bs, lx.es, two, Q, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, mult, tid, nthr); \
+        else pp_pass_p2_fused2<RR, BFAST, 1, 0>(X0, X1, lx.bs, lx.es, two, Q, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, mult, tid, nthr); \
+    } else {                                                                                                     \
+        if (lq.pad) pp_pass_p2_fused2<RR, BFAST, 0, 1>(X0, X1, lx.bs, lx.es, two, Q, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, mult, tid, nthr); \
+        else pp_pass_p2_fused2<RR, BFAST, 0, 0>(X0, X1, lx.bs, lx.es, two, Q, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, mult, tid, nthr); \
+    }
+    // (callers use this path only when the last pass has radix <= 8: two
+    // inputs' radix-16 butterflies in registers would spill)
+    if (lr == 3) { FFTLB_F2(8) }
+    else if (lr == 2) { FFTLB_F2(4) }
+    else { FFTLB_F2(2) }
+#undef FFTLB_F2
+    sync();
+}
+
+// adjoint passes L-1 .. 1 between Q0 and Q1 (same layout lq); returns 0 if
+// the result is in Q0, 1 if in Q1
+template <bool BFAST, typename C>
+__device__ int pp_adj_tail_p2(C *Q0, C *Q1, Lay lq, int n, int nbatch, const C *T, int tid, int nthr,
+                              const GroupSync &sync) {
+    const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
+    int where = 0, lr, lns, toff;
+    for (int p = L - 2; p >= 0; --p) {
+        p2_schedule(logn, p, &lr, &lns, &toff);
+        C *src = where ? Q1 : Q0, *dst = where ? Q0 : Q1;
+        if (lq.pad) pp_pass_p2_adj_r<BFAST, 1, 1>(lr, src, lq.bs, lq.es, dst, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        else pp_pass_p2_adj_r<BFAST, 0, 0>(lr, src, lq.bs, lq.es, dst, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        sync();
+        where ^= 1;
+    }
+    return where;
+}
+
 // Dispatch: the shift-based passes when n (and, for BFAST, nbatch) is a
 // power of two, the generic passes otherwise.  PADA / PADB must match
 // la.pad / lb.pad.

@@ -361,6 +361,23 @@ template <typename real> struct ColMult {
     }
 };
 
+// output o of a derivative group: sum over its terms of M_term(k_x, k_y)
+// times input term_in, times the inverse normalisation (the per-element
+// form of col_multiply, for pp_out_fused_p2)
+template <typename real> struct GroupMult {
+    using C = typename cplx_of<real>::type;
+    real p[5], q[5], scale;
+    int two, in0, in1;
+    const real *kxs, *kys;
+    int kx0;
+    __device__ __forceinline__ C operator()(int b, int e, C x0, C x1) const {
+        const real ax = kxs[kx0 + b], ay = kys[e];
+        C acc = mult_apply<real>(p[0], p[1], p[2], p[3], p[4], ax, ay, in0 ? x1 : x0);
+        if (two) acc = cadd(acc, mult_apply<real>(q[0], q[1], q[2], q[3], q[4], ax, ay, in1 ? x1 : x0));
+        return cscale(acc, scale);
+    }
+};
+
 template <typename C>
 __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDesc *groups, int k, int ntiles,
                                            int ngroups, int TW, int ny, int BOXR, const CUtensorMap *tmap) {
@@ -489,9 +506,44 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 gout[(size_t)e * h + c] = R[lr(c, e)];
             }
         } else {
+            C *in1 = in0 + tile;
+            if (pow2ny && kx0 != 0 && (ilog2(ny) & 3) != 0) {   // last pass radix <= 8
+                // inputs: forward passes 1 .. L-1 (X0 in {in0, wk0}, X1 in
+                // {in1, wk1}); each output: one fused pass into the free pair
+                // of buffers, then the adjoint passes L-1 .. 1
+                const GroupSync bs{0, NT};
+                const int wx = pp_fwd_head_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, tid, NT, bs);
+                if (gd.nin > 1) pp_fwd_head_p2<true>(in1, lt, wk1, lw, ny, TW, Tc, tid, NT, bs);
+                const C *X0 = wx ? wk0 : in0, *X1 = wx ? wk1 : in1;
+                const Lay lx = wx ? lw : lt;
+                C *Q0 = wx ? in0 : wk0, *Q1 = wx ? in1 : wk1;
+                const Lay lq = wx ? lt : lw;
+                for (int o = 0; o < gd.nout; ++o) {
+                    GroupMult<real> m;
+                    for (int j = 0; j < 5; ++j) {
+                        m.p[j] = (real)gd.c[o][0][j];
+                        m.q[j] = (real)gd.c[o][1][j];
+                    }
+                    m.scale = scale;
+                    m.two = gd.nterm[o] > 1;
+                    m.in0 = gd.term_in[o][0];
+                    m.in1 = gd.term_in[o][1];
+                    m.kxs = kxs;
+                    m.kys = kys;
+                    m.kx0 = kx0;
+                    pp_out_fused_p2<true>(X0, X1, lx, gd.nin > 1, Q0, lq, ny, TW, Tc, m, tid, NT, bs);
+                    const int wq = pp_adj_tail_p2<true>(Q0, Q1, lq, ny, TW, Tc, tid, NT, bs);
+                    const C *R = wq ? Q1 : Q0;
+                    gout = spec_r + (size_t)gd.out_slot[o] * slot + kx0;
+                    for (int idx = tid; idx < tile; idx += NT) {
+                        const int e = idx >> lgTW, c = idx & (TW - 1);
+                        gout[(size_t)e * h + c] = R[lq(c, e)];
+                    }
+                    __syncthreads();
+                }
+            } else {
             // X0 in {in0, wk0}, X1 in {in1, wk1}; outputs ping-pong between
             // the two buffers left free
-            C *in1 = in0 + tile;
             const int w0 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
             C *X0 = w0 ? wk0 : in0;
             C *F0 = w0 ? in0 : wk0;
@@ -521,6 +573,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                     gout[(size_t)e * h + c] = R[lr(c, e)];
                 }
                 __syncthreads();
+            }
             }
         }
         fence_proxy_async();
