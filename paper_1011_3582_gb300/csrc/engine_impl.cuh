@@ -2,24 +2,28 @@
 // and the per-precision plan.  Included by engine_f64.cu and engine_f32.cu
 // only (each instantiates one precision).
 //
-// One Runge-Kutta stage L(f) (Eq. 10) runs as six launches on the handle's
-// stream:
-//   K1 row_forward_moments  moments rho, u, T (Eqs. 7-9) of the stage state,
-//                           level-1 fields Pi = P^w - rho T (Eq. 18) and
-//                           g = M/T; forward row transforms of the 32 moving
-//                           f_i and of rho, u_x, u_y, T, Pi, g
-//   K2 col (convection)     column forward -> i (v_x k_m,x + v_y k_m,y) ->
-//                           column inverse for the 32 f_i (in place)
-//   K2 col (level 1)        15 derivative spectra of rho, u, T, Pi, g
-//   K3 row_level1           row inverse of the 15 derivatives; Lambda (Eq. 19),
-//                           Phi = 2 q rho T grad T (Eq. 23), the numerator of
-//                           C (Eq. 22) and of B (Eq. 21); forward row
-//                           transforms of Lambda_xx, Lambda_xy, Lambda_yy,
-//                           Phi_x, Phi_y
-//   K2 col (level 2)        d_b Lambda_xb, d_b Lambda_yb, d_a Phi_a
-//   K5 row_final            row inverse of the convection terms and level-2
+// One Runge-Kutta stage L(f) (Eq. 10) runs as six launches of the
+// pipelined kernels of kernels_pipe.cuh on the handle's stream (profile
+// names in parentheses):
+//   k1_pipe (row_forward_moments)  moments rho, u, T (Eqs. 7-9) of the stage
+//                           state, level-1 fields Pi = P^w - rho T (Eq. 18)
+//                           and g = M/T; forward row transforms of the 32
+//                           moving f_i and of rho, u_x, u_y, T, Pi, g
+//   kcol_pipe (col_convection)  column forward -> i (v_x k_m,x + v_y k_m,y)
+//                           -> column inverse for the 32 f_i (in place)
+//   kcol_pipe (col_level1)  15 derivative spectra of rho, u, T, Pi, g
+//   k3_pipe (row_level1)    row inverse of the 15 derivatives; Lambda
+//                           (Eq. 19), Phi = 2 q rho T grad T (Eq. 23), the
+//                           numerators of C (Eq. 22) and B (Eq. 21); forward
+//                           row transforms of Lambda_xx, Lambda_xy,
+//                           Lambda_yy, Phi_x, Phi_y
+//   kcol_pipe (col_level2)  d_b Lambda_xb, d_b Lambda_yb, d_a Phi_a
+//   k5_pipe (row_final)     row inverse of the convection terms and level-2
 //                           divergences; A, B, C, C_q (Eqs. 20-23), f^eq
 //                           (Eq. 3), I (Eq. 11), BGK and the RK combination.
+// This file holds the engine (plan, tables, launches) and the auxiliary
+// kernels of the per-run calls: equilibrium initialisation, moments,
+// conversions, and the gradient / invariant transforms.
 //
 // Spectra are stored one-sided: slot s holds [ny][nx/2] complex values of
 // a row-transformed (and later column-transformed) field, with the real
@@ -143,99 +147,8 @@ __device__ __forceinline__ void weights_Fk(real T, real F[5]) {
 }
 
 // ---------------------------------------------------------------------------
-// K1: moments + forward row transforms
-// ---------------------------------------------------------------------------
-
-template <typename real>
-__global__ void __launch_bounds__(NT) k_row_forward_moments(const real *__restrict__ f,
-                                                            typename cplx_of<real>::type *__restrict__ spec,
-                                                            real *__restrict__ fields,
-                                                            const typename cplx_of<real>::type *__restrict__ Wr_g,
-                                                            const typename cplx_of<real>::type *__restrict__ Wp_g,
-                                                            KP<real> P, int B) {
-    using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
-    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
-    C *Wr = reinterpret_cast<C *>(smem_raw);
-    C *Wp = Wr + h;
-    C *buf = Wp + h;
-    real *acc = reinterpret_cast<real *>(buf + (size_t)B * h);   // [4][nx]
-    load_tables(Wr, Wr_g, h);
-    load_tables(Wp, Wp_g, h);
-    const real *frow = f + (size_t)y * nx;
-    for (int x = tid; x < nx; x += NT) {
-        real v = frow[x];   // rest velocity: only the mass moment
-        acc[x] = v;
-        acc[nx + x] = 0;
-        acc[2 * nx + x] = 0;
-        acc[3 * nx + x] = 0;
-    }
-    real *bre = reinterpret_cast<real *>(buf);
-    for (int i0 = 1; i0 < Q; i0 += B) {
-        const int nb = min(B, Q - i0);
-        for (int r = 0; r < nb; ++r) {
-            const int i = i0 + r;
-            const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
-            const real *fi = f + (size_t)i * N + (size_t)y * nx;
-            for (int x = tid; x < nx; x += NT) {
-                real v = fi[x];
-                acc[x] += v;
-                acc[nx + x] += vx * v;
-                acc[2 * nx + x] += vy * v;
-                acc[3 * nx + x] += v2 * v;
-                bre[(size_t)r * nx + x] = v;
-            }
-        }
-        rows_r2c(buf, h, nb, Wr, Wp);
-        for (int r = 0; r < nb; ++r) {
-            C *dst = spec + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
-            for (int k = tid; k < h; k += NT) dst[k] = buf[(size_t)r * h + k];
-        }
-        __syncthreads();
-    }
-    // moments (Eqs. 7-9): rho T = (sum |v|^2 f - rho |u|^2) / 2
-    for (int x = tid; x < nx; x += NT) {
-        real rho = acc[x];
-        real ux = acc[nx + x] / rho, uy = acc[2 * nx + x] / rho;
-        real T = real(0.5) * (acc[3 * nx + x] / rho - (ux * ux + uy * uy));
-        acc[x] = rho;
-        acc[nx + x] = ux;
-        acc[2 * nx + x] = uy;
-        acc[3 * nx + x] = T;
-        fields[(size_t)y * nx + x] = rho;
-        fields[N + (size_t)y * nx + x] = ux;
-        fields[2 * N + (size_t)y * nx + x] = uy;
-        fields[3 * N + (size_t)y * nx + x] = T;
-    }
-    // level-1 fields rho, ux, uy, T, Pi, g
-    for (int j0 = 0; j0 < 6; j0 += B) {
-        const int nb = min(B, 6 - j0);
-        for (int r = 0; r < nb; ++r) {
-            const int j = j0 + r;
-            for (int x = tid; x < nx; x += NT) {
-                real v;
-                if (j < 4) {
-                    v = acc[(size_t)j * nx + x];
-                } else {
-                    real rho = acc[x], T = acc[3 * nx + x];
-                    if (j == 4) v = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;   // Eq. 18
-                    else v = (P.K + P.H * T) / T;                                               // M / T
-                }
-                bre[(size_t)r * nx + x] = v;
-            }
-        }
-        rows_r2c(buf, h, nb, Wr, Wp);
-        for (int r = 0; r < nb; ++r) {
-            C *dst = spec + (size_t)(SLOT_RHO + j0 + r) * slot + (size_t)y * h;
-            for (int k = tid; k < h; k += NT) dst[k] = buf[(size_t)r * h + k];
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K2: column pass  forward -> multiplier -> inverse
+// column pass for the gradient and the invariants (one tile per block):
+// forward -> multiplier -> inverse
 // ---------------------------------------------------------------------------
 
 template <typename real>
@@ -322,189 +235,6 @@ __global__ void __launch_bounds__(NT) k_col(typename cplx_of<real>::type *__rest
         for (int idx = tid; idx < tile; idx += NT) {
             const int c = idx % TW, yy = idx / TW;
             dst[(size_t)yy * h + kx0 + c] = work[c * ny + yy];
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K3: level-1 derivatives -> Lambda, Phi, C and B numerators -> forward rows
-// ---------------------------------------------------------------------------
-
-template <typename real>
-__global__ void __launch_bounds__(NT) k_row_level1(typename cplx_of<real>::type *__restrict__ spec,
-                                                   const real *__restrict__ fields, real *__restrict__ aux,
-                                                   const typename cplx_of<real>::type *__restrict__ Wr_g,
-                                                   const typename cplx_of<real>::type *__restrict__ Wp_g,
-                                                   KP<real> P) {
-    using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
-    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
-    C *Wr = reinterpret_cast<C *>(smem_raw);
-    C *Wp = Wr + h;
-    C *d = Wp + h;   // [15][h]
-    load_tables(Wr, Wr_g, h);
-    load_tables(Wp, Wp_g, h);
-    for (int o = 0; o < ND1; ++o) {
-        const C *src = spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h;
-        for (int k = tid; k < h; k += NT) d[(size_t)o * h + k] = src[k];
-    }
-    rows_c2r(d, h, ND1, Wr, Wp);
-    __syncthreads();
-    const real *dr = reinterpret_cast<const real *>(d);
-    real *dw = reinterpret_cast<real *>(d);
-    for (int x = tid; x < nx; x += NT) {
-        const size_t s = (size_t)y * nx + x;
-        const real rho = fields[s], T = fields[3 * N + s];
-        const real rx = dr[D_RX * nx + x], ry = dr[D_RY * nx + x], lap = dr[D_LAP * nx + x];
-        const real uxx = dr[D_UXX * nx + x], uxy = dr[D_UXY * nx + x];
-        const real uyx = dr[D_UYX * nx + x], uyy = dr[D_UYY * nx + x];
-        const real divx = dr[D_DIVX * nx + x], divy = dr[D_DIVY * nx + x];
-        const real Tx = dr[D_TX * nx + x], Ty = dr[D_TY * nx + x];
-        const real Pix = dr[D_PIX * nx + x], Piy = dr[D_PIY * nx + x];
-        const real gx = dr[D_GX * nx + x], gy = dr[D_GY * nx + x];
-        const real M = P.K + P.H * T;
-        const real Pi = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;
-        // Eq. 19
-        const real grad2 = rx * rx + ry * ry;
-        const real iso = -(rho * T * (rx * gx + ry * gy)) - M * (rho * lap + real(0.5) * grad2);
-        const real Lxx = M * rx * rx + iso, Lxy = M * rx * ry, Lyy = M * ry * ry + iso;
-        // Eq. 22 numerator (without C_q)
-        const real div = uxx + uyy;
-        const real Ldu = Lxx * uxx + Lxy * (uyx + uxy) + Lyy * uyy;
-        const real Cn = Pi * div + Ldu - P.zeta * div * div + P.a * rho * rho * div +
-                        P.K * (real(-0.5) * grad2 * div - rho * (rx * divx + ry * divy) -
-                               (rx * (uxx * rx + uyx * ry) + ry * (uxy * rx + uyy * ry)));
-        aux[s] = Cn;
-        aux[N + s] = Pix - P.zeta * divx;   // Eq. 21 numerator without d_b Lambda_ab
-        aux[2 * N + s] = Piy - P.zeta * divy;
-        const real q2 = real(2) * P.q * rho * T;   // Eq. 23: Phi = 2 q rho T grad T
-        dw[0 * nx + x] = Lxx;
-        dw[1 * nx + x] = Lxy;
-        dw[2 * nx + x] = Lyy;
-        dw[3 * nx + x] = q2 * Tx;
-        dw[4 * nx + x] = q2 * Ty;
-    }
-    rows_r2c(d, h, 5, Wr, Wp);
-    for (int r = 0; r < 5; ++r) {
-        C *dst = spec + (size_t)(SLOT_L2 + r) * slot + (size_t)y * h;
-        for (int k = tid; k < h; k += NT) dst[k] = d[(size_t)r * h + k];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K5: convection + level-2 -> coefficients -> f^eq, I, BGK, RK combination
-// ---------------------------------------------------------------------------
-
-constexpr int NST = 16;   // per-site state kept in shared memory
-
-template <typename real>
-__global__ void __launch_bounds__(NT) k_row_final(const typename cplx_of<real>::type *__restrict__ spec,
-                                                  const real *__restrict__ fields, const real *__restrict__ aux,
-                                                  const real *fcur, const real *fbase, real *fout, real alpha,
-                                                  real beta, const typename cplx_of<real>::type *__restrict__ Wr_g,
-                                                  const typename cplx_of<real>::type *__restrict__ Wp_g, KP<real> P,
-                                                  int B) {
-    using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
-    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
-    C *Wr = reinterpret_cast<C *>(smem_raw);
-    C *Wp = Wr + h;
-    C *l2 = Wp + h;                         // [3][h]
-    C *cb = l2 + (size_t)3 * h;              // [B][h]
-    real *st = reinterpret_cast<real *>(cb + (size_t)B * h);   // [NST][nx]
-    load_tables(Wr, Wr_g, h);
-    load_tables(Wp, Wp_g, h);
-    const int l2slots[3] = {SLOT_L2 + 0, SLOT_L2 + 2, SLOT_L2 + 3};
-    for (int r = 0; r < 3; ++r) {
-        const C *src = spec + (size_t)l2slots[r] * slot + (size_t)y * h;
-        for (int k = tid; k < h; k += NT) l2[(size_t)r * h + k] = src[k];
-    }
-    rows_c2r(l2, h, 3, Wr, Wp);
-    const real *l2r = reinterpret_cast<const real *>(l2);
-    for (int x = tid; x < nx; x += NT) {
-        const size_t s = (size_t)y * nx + x;
-        const real rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
-        const real rT = rho * T;
-        const real inv2 = real(1) / (real(2) * rho * T * T);
-        const real Bx = (aux[N + s] + l2r[x]) / rT;            // Eq. 21
-        const real By = (aux[2 * N + s] + l2r[nx + x]) / rT;
-        const real Cc = aux[s] * inv2;                           // Eq. 22
-        const real Cq = l2r[2 * nx + x] * inv2;                  // Eq. 23
-        const real CC = Cc + Cq;
-        const real A = real(-2) * CC * T;                        // Eq. 20
-        const real u2 = ux * ux + uy * uy;
-        real F[5];
-        weights_Fk<real>(T, F);                                  // Eqs. 4-6
-        const real iT = real(1) / T;
-        const real qq = real(0.5) * u2 * iT;                     // u^2 / 2T
-        const real om = real(1) - qq;
-        st[0 * nx + x] = rho * F[0];
-        st[1 * nx + x] = rho * F[1];
-        st[2 * nx + x] = rho * F[2];
-        st[3 * nx + x] = rho * F[3];
-        st[4 * nx + x] = rho * F[4];
-        st[5 * nx + x] = om + real(0.5) * qq * qq;               // 1 - u^2/2T + u^4/8T^2
-        st[6 * nx + x] = om * iT;
-        st[7 * nx + x] = real(0.5) * om * iT * iT;
-        st[8 * nx + x] = iT * iT * iT / real(6);
-        st[9 * nx + x] = iT * iT * iT * iT / real(24);
-        st[10 * nx + x] = ux;
-        st[11 * nx + x] = uy;
-        // I = -(A + B.(v-u) + CC |v-u|^2) f^eq = -(e0 + e1.v + CC |v|^2) f^eq
-        st[12 * nx + x] = A - (Bx * ux + By * uy) + CC * u2;
-        st[13 * nx + x] = Bx - real(2) * CC * ux;
-        st[14 * nx + x] = By - real(2) * CC * uy;
-        st[15 * nx + x] = CC;
-    }
-    __syncthreads();
-    const real dt = P.dt, itau = real(1) / P.tau;
-    const real *cr = reinterpret_cast<const real *>(cb);
-    // rest velocity (no convection)
-    for (int x = tid; x < nx; x += NT) {
-        const size_t s = (size_t)y * nx + x;
-        const real fe = st[0 * nx + x] * st[5 * nx + x];
-        const real I = -st[12 * nx + x] * fe;
-        const real fc = fcur[s];
-        const real rhs = -(fc - fe) * itau + I;
-        real fn = beta * (fc + dt * rhs);
-        if (alpha != real(0)) fn += alpha * fbase[s];
-        fout[s] = fn;
-    }
-    for (int i0 = 1; i0 < Q; i0 += B) {
-        const int nb = min(B, Q - i0);
-        for (int r = 0; r < nb; ++r) {
-            const C *src = spec + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
-            for (int k = tid; k < h; k += NT) cb[(size_t)r * h + k] = src[k];
-        }
-        rows_c2r(cb, h, nb, Wr, Wp);
-        for (int x = tid; x < nx; x += NT) {
-            real sv[NST];
-#pragma unroll
-            for (int e = 0; e < NST; ++e) sv[e] = st[e * nx + x];
-            for (int r = 0; r < nb; ++r) {
-                const int i = i0 + r;
-                const size_t s = (size_t)i * N + (size_t)y * nx + x;
-                const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
-                const int k = c_ring[i];
-                const real vu = vx * sv[10] + vy * sv[11];
-                const real br = sv[5] + vu * (sv[6] + vu * (sv[7] + vu * (sv[8] + vu * sv[9])));
-                real rF = sv[0];
-                rF = (k == 1) ? sv[1] : rF;
-                rF = (k == 2) ? sv[2] : rF;
-                rF = (k == 3) ? sv[3] : rF;
-                rF = (k == 4) ? sv[4] : rF;
-                const real fe = rF * br;                                   // Eq. 3
-                const real I = -(sv[12] + sv[13] * vx + sv[14] * vy + sv[15] * v2) * fe;   // Eq. 11
-                const real fc = fcur[s];
-                const real conv = cr[(size_t)r * nx + x];
-                const real rhs = -conv - (fc - fe) * itau + I;             // Eq. 10
-                real fn = beta * (fc + dt * rhs);
-                if (alpha != real(0)) fn += alpha * fbase[s];
-                fout[s] = fn;
-            }
         }
         __syncthreads();
     }
@@ -916,8 +646,7 @@ class EngineT : public Engine {
     int conv_groups_ = 0, l1_groups_ = 0, l2_groups_ = 0, grad_groups_ = 0, inv_groups_ = 0;
     // launch configuration
     int TW_ = 1;
-    size_t smem_k1_ = 0, smem_k3_ = 0, smem_k5_ = 0, smem_col1_ = 0, smem_col2_ = 0, smem_rows1_ = 0, smem_inv_ = 0;
-    int B1_ = 1, B5_ = 1;
+    size_t smem_col1_ = 0, smem_col2_ = 0, smem_rows1_ = 0, smem_inv_ = 0;
     // pipelined kernels
     int *err_ = nullptr;
     int nsm_ = 1;
@@ -1328,27 +1057,11 @@ class EngineT : public Engine {
         }
         smem_col1_ = (size_t)(ny_ + 2 * TW_ * ny_) * cs;
         smem_col2_ = (size_t)(ny_ + 3 * TW_ * ny_) * cs;
-        B1_ = std::max(1, std::min(32, (16 * NT) / h_));
-        smem_k1_ = (size_t)(2 * h_ + B1_ * h_) * cs + 4 * nx_ * rs;
-        while (smem_k1_ > budget && B1_ > 1) {
-            --B1_;
-            smem_k1_ = (size_t)(2 * h_ + B1_ * h_) * cs + 4 * nx_ * rs;
-        }
-        smem_k3_ = (size_t)(2 * h_ + ND1 * h_) * cs;
-        B5_ = std::max(1, std::min(32, (16 * NT) / h_));
-        smem_k5_ = (size_t)(2 * h_ + 3 * h_ + B5_ * h_) * cs + NST * nx_ * rs;
-        while (smem_k5_ > budget && B5_ > 1) {
-            --B5_;
-            smem_k5_ = (size_t)(2 * h_ + 3 * h_ + B5_ * h_) * cs + NST * nx_ * rs;
-        }
         smem_rows1_ = (size_t)3 * h_ * cs;
         smem_inv_ = (size_t)4 * h_ * cs;
-        if (smem_k1_ > budget || smem_k3_ > budget || smem_k5_ > budget || smem_col2_ > budget)
+        if (smem_col2_ > budget || smem_inv_ > budget)
             return Status::err(FFTLB_ERR_ARG, "grid too large for shared-memory tiles");
-        FFTLB_CU(cudaFuncSetAttribute(k_row_forward_moments<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
         FFTLB_CU(cudaFuncSetAttribute(k_col<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
-        FFTLB_CU(cudaFuncSetAttribute(k_row_level1<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
-        FFTLB_CU(cudaFuncSetAttribute(k_row_final<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
         kp_.nx = nx_;
         kp_.ny = ny_;
         kp_.h = h_;
