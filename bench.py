@@ -232,6 +232,44 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+class Replicas:
+    """Bookkeeping of a multi-GPU run launched by torch.distributed.run: one
+    process per GPU, each running its own replica of the workload (the
+    single-grid step does not shard: every transform is global).  barrier()
+    aligns the ranks around a timed region, maxed(t) is the maximum over
+    ranks (the whole job's time), and a whole-job throughput is
+    world x (units per rank) / maxed(time)."""
+
+    def __init__(self, backend, device):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def maxed(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, units_per_rank, seconds):
+        return self.world * units_per_rank / seconds
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,10 +307,7 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    rep = Replicas("nccl", "cuda")
 
     import __graft_entry__
     __graft_entry__.build()
@@ -281,17 +316,7 @@ def main():
     n = args.grid
     stream = torch.cuda.current_stream()
     fields = workload_fields(n)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def maxed(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, maxed = rep.barrier, rep.maxed
 
     def time_path(precision, steps, warmup, sample_clocks):
         clk = ClockSampler(local)
@@ -333,7 +358,7 @@ def main():
     tuned = {}
     ms, prof, inv, lps, clocks = time_path(args.precision, args.steps, args.warmup, True)
     K = args.steps
-    value = world * n * n * K / (ms * 1e-3) / 1e6
+    value = rep.throughput(n * n * K, ms * 1e-3) / 1e6
 
     peaks, peak_kind = measured_peaks()
     top = max(prof, key=lambda k: prof[k][0])
@@ -462,8 +487,7 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
                 "fp64": fp64, "sweep": sweep, "cufft_reference": cufft, "invariants_after": inv}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
 
 
 if __name__ == "__main__":
