@@ -3,7 +3,7 @@
  * state).  A small convolutional network maps an early-time density and
  * temperature field, and the run temperature, to a later state of the same
  * run; the plain method (fftlb_step) continues from it.  The network is not
- * part of the paper; the method remains the judge of its error.
+ * part of the paper; the method itself measures its error.
  *
  * Network (all spatial operations periodic, like the FFT-LB grid):
  *   input    X [3][H][W] float32:  X0 = s_rho (rho / rho_c - 1),

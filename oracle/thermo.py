@@ -1,4 +1,4 @@
-"""Equilibrium thermodynamics of the van der Waals fluid used to judge runs of
+"""Equilibrium thermodynamics of the van der Waals fluid used to check runs of
 the FFT-LB method (arXiv:1011.3582, Sec. 4).
 
 TEST INFRASTRUCTURE ONLY (see oracle/fftlb_oracle.py).  FP64, scipy root
