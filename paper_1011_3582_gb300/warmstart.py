@@ -121,11 +121,13 @@ def train(fl, net, data, steps=2000, lr=2e-3, seed=0, log=print):
     return hist
 
 
-def compare(fl, net, n, Tr, seed, max_steps=200000):
-    """Cold and warm steps from T_IN to onset, and their wall times."""
+def compare(fl, net, n, Tr, seed, max_steps=200000, cold_precision=32):
+    """Cold and warm steps from T_IN to onset, and their wall times.  The
+    warm run is the mixed path (fp32 method, bf16 network); the cold run
+    uses the method in cold_precision (32 or 64)."""
     import torch
-    out = dict(n=n, T_r=Tr, seed=seed)
-    with fl.Handle(run_params(fl, n)) as h:
+    out = dict(n=n, T_r=Tr, seed=seed, cold_precision=cold_precision)
+    with fl.Handle(run_params(fl, n, cold_precision)) as h:
         start(fl, h, n, Tr, seed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -161,6 +163,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--eval", default="512:0.6:21,512:0.7:22,512:0.675:23")
     ap.add_argument("--out", default="warmstart_out")
+    ap.add_argument("--params", default=None, help="skip training: evaluate these parameters (.npy)")
+    ap.add_argument("--cold-precision", type=int, default=32, choices=[32, 64])
     a = ap.parse_args(argv)
     os.makedirs(a.out, exist_ok=True)
     logf = open(os.path.join(a.out, "log.jsonl"), "w")
@@ -170,22 +174,25 @@ def main(argv=None):
         logf.write(msg + "\n")
         logf.flush()
 
-    with fl.CNN(a.n, a.n) as net:
-        net.set_params(init_params(0))
-        data = generate(fl, net, a.n, [float(t) for t in a.temps.split(",")], [int(s) for s in a.seeds.split(",")],
-                        log=log)
-        t0 = time.time()
-        train(fl, net, data, a.train_steps, a.lr, log=log)
-        log(json.dumps(dict(train_s=round(time.time() - t0, 1))))
-        params = net.get_params()
-    np.save(os.path.join(a.out, "warmstart_params.npy"), params)
+    if a.params:
+        params = np.load(a.params)
+    else:
+        with fl.CNN(a.n, a.n) as net:
+            net.set_params(init_params(0))
+            data = generate(fl, net, a.n, [float(t) for t in a.temps.split(",")],
+                            [int(s) for s in a.seeds.split(",")], log=log)
+            t0 = time.time()
+            train(fl, net, data, a.train_steps, a.lr, log=log)
+            log(json.dumps(dict(train_s=round(time.time() - t0, 1))))
+            params = net.get_params()
+        np.save(os.path.join(a.out, "warmstart_params.npy"), params)
     results = []
     for spec in a.eval.split(","):
         n, Tr, seed = spec.split(":")
         n = int(n)
         with fl.CNN(n, n) as net:
             net.set_params(params)
-            r = compare(fl, net, n, float(Tr), int(seed))
+            r = compare(fl, net, n, float(Tr), int(seed), cold_precision=a.cold_precision)
         results.append(r)
         log(json.dumps(r))
     json.dump(results, open(os.path.join(a.out, "results.json"), "w"), indent=1)
