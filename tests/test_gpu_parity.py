@@ -207,3 +207,34 @@ def test_torch_cufft_reference_matches_oracle():
     err = (np.abs(f_t - f_o) / np.abs(f_o)).max()
     print(f"torch/cuFFT fp32 256^2 after 3 RK3 steps: max |df|/f = {err:.3e} (bound {bound:.3e})")
     assert err < bound
+
+
+@functools.lru_cache(maxsize=None)
+def _droplet512_oracle():
+    from oracle import thermo as TH
+    n, T = 512, 0.8 * TC49
+    rv, rl = TH.maxwell(T, A49, B21)
+    kw = dict(nx=n, ny=n, a=A49, b=B21)
+    fields = W.droplet(n, n, 80, rl, rv, T, width=2.0)
+    p = oracle_params(kw, integrator=3)
+    return fields, kw, O.run(O.init_equilibrium(*fields, p), p, 1)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_droplet_512_precision_config(fl, precision):
+    """The precision configuration's droplet (512^2, R = 80, Maxwell
+    densities at T = 0.8 T_c, tanh width 2), one SSP-RK3 step, element by
+    element against the oracle: fp64 within 1e-9, fp32 within
+    fp32_force_bound."""
+    fields, kw, f_o = _droplet512_oracle()
+    with fl.Handle(fl.params(integrator=3, precision=precision, **kw)) as h:
+        h.set_fields(*fields)
+        h.step(1)
+        f_g = h.get_f()
+    if precision == 64:
+        assert rel_err(f_g, f_o) < 1e-9
+    else:
+        bound = fp32_force_bound(512, 1, fields[0], fields[3])
+        err = (np.abs(f_g - f_o) / np.abs(f_o)).max()
+        print(f"fp32 512^2 droplet after 1 RK3 step: max |df|/f = {err:.3e} (bound {bound:.3e})")
+        assert err < bound
