@@ -651,7 +651,7 @@ class EngineT : public Engine {
     int *err_ = nullptr;
     int nsm_ = 1;
     int CH1_ = 8, SMAX1_ = 1, grid1_ = 1, NHB5_ = 1, WR3_ = 1, CH5_ = 8, grid5_ = 1, SMAX5_ = 1, BOXR_ = 1;
-    int TWc_ = 1, TWl_ = 1, gridc_ = 1, gridl_ = 1;
+    int TWc_ = 1, TWl_ = 1, gridc_ = 1, gridl_ = 1, NBUFc_ = 2, NBUFl_ = 2;
     size_t smem1_ = 0, smem3_ = 0, smem5_ = 0, smemc_ = 0, smeml_ = 0;
     CUtensorMap tmap_conv_{}, tmap_l1_{};
     // profiling
@@ -1121,6 +1121,36 @@ class EngineT : public Engine {
     size_t budget_ = 0;
     static constexpr int NT1 = KCfg<real, KS_K1>::NT, NTC = KCfg<real, KS_COL>::NT, NT5 = KCfg<real, KS_K5>::NT;
     int ntrmax() const { return std::max(ntr_, ntr8_); }
+    // shared memory of the column kernel: twiddles, pass tables, k tables,
+    // nbuf staged tiles of NIN inputs, NIN padded work tiles
+    size_t col_smem(bool multi, int tw, int nbuf) const {
+        const size_t cs = sizeof(C), rs = sizeof(real), pny = (size_t)padded_len(ny_);
+        const size_t tile = (size_t)tw * ny_ * cs, ptile = (size_t)tw * pny * cs, kt = (h_ + 1 + ny_) * rs;
+        const size_t nin = multi ? 2 : 1;
+        return nbuf > 1 ? (multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, nin * tile, ptile, ptile})
+                                 : smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, nin * tile, ptile}))
+                        : (multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, ptile, ptile})
+                                 : smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, ptile}));
+    }
+    // buffers for a column tile width: two unless one gives more blocks per SM
+    Status col_nbuf(bool multi, int tw, int *nbuf, size_t *sm, int *grid) {
+        int best = -1;
+        for (int nb2 = 2; nb2 >= 1; --nb2) {
+            const size_t s = col_smem(multi, tw, nb2);
+            if (s > budget_) continue;
+            int nb = 0;
+            Status st = multi ? occupancy(kcol_pipe<real, true>, NTC, s, &nb) : occupancy(kcol_pipe<real, false>, NTC, s, &nb);
+            if (!st.good()) return st;
+            if (nb > best) {
+                best = nb;
+                *nbuf = nb2;
+                *sm = s;
+                *grid = std::max(1, nb) * nsm_;
+            }
+        }
+        if (best < 1) return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
+        return Status::ok();
+    }
     // largest row radix for a kernel transforming `rows` rows at a time with
     // nthr threads: radix 16 unless its passes would leave threads idle
     int row_maxlr(int rows, int nthr) const { return rows * (h_ / 16) < nthr ? 3 : 4; }
@@ -1192,34 +1222,35 @@ class EngineT : public Engine {
                 break;
             }
         const size_t pny = (size_t)padded_len(ny_);
-        auto pick_tw = [&](bool multi, int *tw_out, size_t *sm_out, int *grid_out) -> Status {
-            int bestnb = 0;
+        auto pick_tw = [&](bool multi, int *tw_out, int *nbuf_out, size_t *sm_out, int *grid_out) -> Status {
+            int bestscore = -1;
             *tw_out = 0;
             for (int tw = 8; tw >= 1; tw >>= 1) {
                 if (h_ % tw) continue;
                 if ((2 * tw * rs) % 16) continue;   // tensor box row: whole 16-byte units
-                const size_t tile = (size_t)tw * ny_ * cs, ptile = (size_t)tw * pny * cs;
-                const size_t kt = (h_ + 1 + ny_) * rs;
-                const size_t sm = multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, 2 * tile, 2 * tile, ptile, ptile})
-                                        : smem_bytes({ny_ * cs, ntc_ * cs, kt, tile, tile, ptile});
-                if (sm > budget) continue;
-                Status s2 = multi ? occupancy(kcol_pipe<real, true>, NTC, sm, &nb)
-                                  : occupancy(kcol_pipe<real, false>, NTC, sm, &nb);
-                if (!s2.good()) return s2;
-                if (nb > bestnb) {
-                    bestnb = nb;
-                    *tw_out = tw;
-                    *sm_out = sm;
+                for (int nbuf = 2; nbuf >= 1; --nbuf) {
+                    int nb = 0;
+                    const size_t sm = col_smem(multi, tw, nbuf);
+                    if (sm > budget) continue;
+                    Status s2 = multi ? occupancy(kcol_pipe<real, true>, NTC, sm, &nb)
+                                      : occupancy(kcol_pipe<real, false>, NTC, sm, &nb);
+                    if (!s2.good()) return s2;
+                    // most blocks per SM, then the widest tile, then two buffers
+                    const int score = nb * 1000 + tw * 10 + nbuf;
+                    if (nb > 0 && score > bestscore) {
+                        bestscore = score;
+                        *tw_out = tw;
+                        *nbuf_out = nbuf;
+                        *sm_out = sm;
+                        *grid_out = nb * nsm_;
+                    }
                 }
             }
             if (!*tw_out) return Status::err(FFTLB_ERR_ARG, "grid too large for the column kernel");
-            Status s3 = multi ? occupancy(kcol_pipe<real, true>, NTC, *sm_out, &nb)
-                              : occupancy(kcol_pipe<real, false>, NTC, *sm_out, &nb);
-            *grid_out = std::max(1, nb) * nsm_;
-            return s3;
+            return Status::ok();
         };
-        if (!(st = pick_tw(false, &TWc_, &smemc_, &gridc_)).good()) return st;
-        if (!(st = pick_tw(true, &TWl_, &smeml_, &gridl_)).good()) return st;
+        if (!(st = pick_tw(false, &TWc_, &NBUFc_, &smemc_, &gridc_)).good()) return st;
+        if (!(st = pick_tw(true, &TWl_, &NBUFl_, &smeml_, &gridl_)).good()) return st;
         if (!(st = make_tmap(&tmap_conv_, TWc_)).good()) return st;
         if (!(st = make_tmap(&tmap_l1_, TWl_)).good()) return st;
         // K3 (one row per block, not pipelined inside a block): most blocks
@@ -1310,25 +1341,19 @@ class EngineT : public Engine {
         if (!twok(twc) || !twok(twl) || ch1 < 6 || ch1 > 8 || ch5 < 2 || ch5 > CHMAX5 || (ch5 & 1) || nhb < 1 || nhb > 2)
             return Status::err(FFTLB_ERR_ARG, "tuning parameters out of range");
         const size_t sm1 = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ch1 * nx_ * rs, (size_t)ch1 * nx_ * rs, ch1 * ph * cs});
-        const size_t kt = (h_ + 1 + ny_) * rs;
-        const size_t tc = (size_t)twc * ny_ * cs, ptc = (size_t)twc * pny * cs;
-        const size_t tl = (size_t)twl * ny_ * cs, ptl = (size_t)twl * pny * cs;
-        const size_t smc = smem_bytes({ny_ * cs, ntc_ * cs, kt, tc, tc, ptc});
-        const size_t sml = smem_bytes({ny_ * cs, ntc_ * cs, kt, 2 * tl, 2 * tl, ptl, ptl});
+        size_t smc = 0, sml = 0;
+        int nbc = 2, nbl = 2, gc = 1, gl = 1;
         const size_t head = (size_t)NHEAD * nx_ * rs;
         const size_t sm5 = smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, (size_t)ch5 * nx_ * rs,
                                        (size_t)ch5 * nx_ * rs, (size_t)std::max(ch5, 3) * ph * cs});
-        if (sm1 > budget_ || smc > budget_ || sml > budget_ || sm5 > budget_)
-            return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
+        if (sm1 > budget_ || sm5 > budget_) return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
         Status st;
+        if (!(st = col_nbuf(false, twc, &nbc, &smc, &gc)).good()) return st;
+        if (!(st = col_nbuf(true, twl, &nbl, &sml, &gl)).good()) return st;
         int nb = 0;
         st = occ_k1(sm1, &nb);
         if (!st.good()) return st;
         const int g1 = std::min(B_ * ny_, std::max(1, nb) * nsm_);
-        if (!(st = occupancy(kcol_pipe<real, false>, NTC, smc, &nb)).good()) return st;
-        const int gc = std::max(1, nb) * nsm_;
-        if (!(st = occupancy(kcol_pipe<real, true>, NTC, sml, &nb)).good()) return st;
-        const int gl = std::max(1, nb) * nsm_;
         st = occ_k5(sm5, &nb);
         if (!st.good()) return st;
         const int g5 = std::min(B_ * ny_, std::max(1, nb) * nsm_);
@@ -1337,6 +1362,8 @@ class EngineT : public Engine {
         if (!(st = make_tmap(&ml, twl)).good()) return st;
         TWc_ = twc;
         TWl_ = twl;
+        NBUFc_ = nbc;
+        NBUFl_ = nbl;
         CH1_ = ch1;
         CH5_ = ch5;
         NHB5_ = nhb;
@@ -1425,10 +1452,10 @@ class EngineT : public Engine {
         if (level1)
             kcol_pipe<real, true><<<gridl_, NTC, smeml_, stream_>>>(specb_, groups_ + first, count, kxt_,
                                                                                kyt_, Wc_, Tc_, ntc_, kp_, TWl_, BOXR_,
-                                                                               tmap_l1_, err_);
+                                                                               NBUFl_, tmap_l1_, err_);
         else
             kcol_pipe<real, false><<<gridc_, NTC, smemc_, stream_>>>(
-                specb_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, tmap_conv_, err_);
+                specb_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, NBUFc_, tmap_conv_, err_);
         FFTLB_LAUNCHED("kcol_pipe");
         return Status::ok();
     }

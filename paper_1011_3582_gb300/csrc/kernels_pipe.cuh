@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                                                                const real *__restrict__ kyt,
                                                                const typename cplx_of<real>::type *__restrict__ Wc_g,
                                                                const typename cplx_of<real>::type *__restrict__ Tc_g,
-                                                               int ntc, KP<real> P, int TW, int BOXR,
+                                                               int ntc, KP<real> P, int TW, int BOXR, int nbuf,
                                                                const __grid_constant__ CUtensorMap tmap, int *err) {
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_COL>::NT;
@@ -424,7 +424,9 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
     real *kxs = (real *)sc.take((size_t)(h + 1 + ny) * sizeof(real));   // k_x then k_y tables
     real *kys = kxs + h + 1;
     C *buf0 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
-    C *buf1 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
+    // nbuf = 2: double-buffered (job k + 2 prefetched while job k + 1 runs);
+    // nbuf = 1: one buffer (job k + 1 loaded after job k), for two blocks per SM
+    C *buf1 = nbuf > 1 ? (C *)sc.take((size_t)NIN * tile * sizeof(C)) : buf0;
     C *wk0 = (C *)sc.take((size_t)ptile * sizeof(C));
     C *wk1 = MULTI ? (C *)sc.take((size_t)ptile * sizeof(C)) : nullptr;
     const Lay lt{1, TW, 0}, lw{1, TW, 1};   // staged tile / padded work tile
@@ -443,10 +445,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
     __syncthreads();
     if (tid == 0) {
         if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, ny, BOXR, &tmap);
-        if (njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, ny, BOXR, &tmap);
+        if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, ny, BOXR, &tmap);
     }
     uint32_t par0 = 0, par1 = 0;
-    bool pend0 = njobs > 0, pend1 = njobs > 1;
+    bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1;
     const real scale = P.scale;
     for (int k = 0; k < njobs; ++k) {
         const bool odd = k & 1;
@@ -578,9 +580,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
         }
         fence_proxy_async();
         __syncthreads();
-        if (tid == 0 && k + 2 < njobs) {
-            kcol_issue(in0, bar, groups, k + 2, ntiles, ngroups, TW, ny, BOXR, &tmap);
-            if (odd) pend1 = true;
+        if (tid == 0 && k + nbuf < njobs) {
+            const bool nodd = (k + nbuf) & 1;   // the barrier of job k + nbuf
+            kcol_issue(in0, nodd ? &bar1 : &bar0, groups, k + nbuf, ntiles, ngroups, TW, ny, BOXR, &tmap);
+            if (nodd) pend1 = true;
             else pend0 = true;
         }
     }
