@@ -20,8 +20,11 @@
 // persistent kernels, per precision and kernel kind.  fp32 defaults
 // (measured at 1024^2): the row-forward kernel runs two 256-thread blocks
 // per SM (its 8-row chunks give one radix-16 butterfly per thread; 229 ->
-// 171 us), the column and final row kernels one 512-thread block (two
-// 256-thread blocks: convection columns 256 -> 348 us).
+// 171 us); the column kernels two 256-thread blocks, each with a single
+// staged tile, so that one block's barrier waits and tile loads overlap the
+// other's passes (convection 227 -> 212 us, level 1 144 -> 129 us against
+// one double-buffered 512-thread block); the final row kernel one 512-thread
+// block (its per-site epilogue needs the registers).
 #ifndef FFTLB_NT32_K1
 #define FFTLB_NT32_K1 256
 #endif
@@ -29,10 +32,10 @@
 #define FFTLB_MINB32_K1 2
 #endif
 #ifndef FFTLB_NT32_COL
-#define FFTLB_NT32_COL 512
+#define FFTLB_NT32_COL 256
 #endif
 #ifndef FFTLB_MINB32_COL
-#define FFTLB_MINB32_COL 1
+#define FFTLB_MINB32_COL 2
 #endif
 #ifndef FFTLB_NT32_K5
 #define FFTLB_NT32_K5 512
