@@ -651,7 +651,7 @@ class EngineT : public Engine {
     int *err_ = nullptr;
     int nsm_ = 1;
     int CH1_ = 8, SMAX1_ = 1, grid1_ = 1, NHB5_ = 1, WR3_ = 1, CH5_ = 8, grid5_ = 1, SMAX5_ = 1, BOXR_ = 1;
-    int TWc_ = 1, TWl_ = 1, gridc_ = 1, gridl_ = 1, NBUFc_ = 2, NBUFl_ = 2;
+    int TWc_ = 1, TWl_ = 1, gridc_ = 1, gridl_ = 1, NBUFc_ = 2, NBUFl_ = 2, NBUF5_ = 2;
     size_t smem1_ = 0, smem3_ = 0, smem5_ = 0, smemc_ = 0, smeml_ = 0;
     CUtensorMap tmap_conv_{}, tmap_l1_{};
     // profiling
@@ -1132,6 +1132,14 @@ class EngineT : public Engine {
                         : (multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, ptile, ptile})
                                  : smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, ptile}));
     }
+    // shared memory of the final row kernel for chunk size ch, nhb head
+    // buffers and nbuf chunk buffers
+    size_t k5_smem(int ch, int nhb, int nbuf) const {
+        const size_t cs = sizeof(C), rs = sizeof(real), ph = (size_t)padded_len(h_);
+        const size_t head = (size_t)NHEAD * nx_ * rs, chunk = (size_t)ch * nx_ * rs;
+        return smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, chunk, nbuf > 1 ? chunk : 0,
+                           (size_t)std::max(ch, 3) * ph * cs});
+    }
     // buffers for a column tile width: two unless one gives more blocks per SM
     Status col_nbuf(bool multi, int tw, int *nbuf, size_t *sm, int *grid) {
         int best = -1;
@@ -1273,25 +1281,24 @@ class EngineT : public Engine {
         }
         if (!WR3_) return Status::err(FFTLB_ERR_ARG, "grid too large for the level-1 row kernel");
         // K5: most blocks per SM first, then two head buffers, then the
-        // largest chunk
+        // largest chunk, then two chunk buffers
         {
             int bestscore = -1;
             CH5_ = 0;
             for (int nhb = 2; nhb >= 1; --nhb) {
                 for (int ch = CHMAX5; ch >= 2; ch -= 2) {
-                    const size_t head = (size_t)NHEAD * nx_ * rs;
-                    const size_t sm =
-                        smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, (size_t)ch * nx_ * rs,
-                                    (size_t)ch * nx_ * rs, (size_t)std::max(ch, 3) * ph * cs});
-                    if (sm > budget) continue;
-                    st = occ_k5(sm, &nb);
-                    if (!st.good()) return st;
-                    const int score = nb * 100 + nhb * 10 + ch;
-                    if (nb > 0 && score > bestscore) {
-                        bestscore = score;
-                        CH5_ = ch;
-                        NHB5_ = nhb;
-                        smem5_ = sm;
+                    for (int nbuf = 2; nbuf >= 1; --nbuf) {
+                        const size_t sm = k5_smem(ch, nhb, nbuf);
+                        if (sm > budget) continue;
+                        if (!(st = occ_k5(sm, &nb)).good()) return st;
+                        const int score = nb * 1000 + nhb * 100 + ch * 10 + nbuf;
+                        if (nb > 0 && score > bestscore) {
+                            bestscore = score;
+                            CH5_ = ch;
+                            NHB5_ = nhb;
+                            NBUF5_ = nbuf;
+                            smem5_ = sm;
+                        }
                     }
                 }
             }
@@ -1343,9 +1350,22 @@ class EngineT : public Engine {
         const size_t sm1 = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ch1 * nx_ * rs, (size_t)ch1 * nx_ * rs, ch1 * ph * cs});
         size_t smc = 0, sml = 0;
         int nbc = 2, nbl = 2, gc = 1, gl = 1;
-        const size_t head = (size_t)NHEAD * nx_ * rs;
-        const size_t sm5 = smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, (size_t)ch5 * nx_ * rs,
-                                       (size_t)ch5 * nx_ * rs, (size_t)std::max(ch5, 3) * ph * cs});
+        // chunk buffers: two unless one gives more blocks per SM
+        int nbuf5 = 0, best5 = -1;
+        size_t sm5 = 0;
+        for (int nb2 = 2; nb2 >= 1; --nb2) {
+            const size_t s5 = k5_smem(ch5, nhb, nb2);
+            if (s5 > budget_) continue;
+            int nb5 = 0;
+            Status s2 = occ_k5(s5, &nb5);
+            if (!s2.good()) return s2;
+            if (nb5 > best5) {
+                best5 = nb5;
+                nbuf5 = nb2;
+                sm5 = s5;
+            }
+        }
+        if (!nbuf5) return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
         if (sm1 > budget_ || sm5 > budget_) return Status::err(FFTLB_ERR_ARG, "tuning parameters exceed shared memory");
         Status st;
         if (!(st = col_nbuf(false, twc, &nbc, &smc, &gc)).good()) return st;
@@ -1367,6 +1387,7 @@ class EngineT : public Engine {
         CH1_ = ch1;
         CH5_ = ch5;
         NHB5_ = nhb;
+        NBUF5_ = nbuf5;
         smem1_ = sm1;
         smemc_ = smc;
         smeml_ = sml;
@@ -1496,13 +1517,13 @@ class EngineT : public Engine {
         const int ml5 = row_maxlr(CH5_, NT5);
         if (SMAX5_ == 1)
             k5_pipe<real, 1><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, ml5, err_);
+                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, NBUF5_, ml5, err_);
         else if (SMAX5_ == 2)
             k5_pipe<real, 2><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, ml5, err_);
+                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, NBUF5_, ml5, err_);
         else
             k5_pipe<real, 4><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
-                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, ml5, err_);
+                                                               Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, NBUF5_, ml5, err_);
         FFTLB_LAUNCHED("k5_pipe");
         return prof_end();
     }

@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
                                                              const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                              const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
-                                                             int ntr, KP<real> P, int CH, int NHB, int maxlr,
+                                                             int ntr, KP<real> P, int CH, int NHB, int nbuf, int maxlr,
                                                              int *err) {
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_K5>::NT;
@@ -760,7 +760,9 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
     real *head0 = (real *)sc.take((size_t)NHEAD * nx * sizeof(real));
     real *head1 = NHB > 1 ? (real *)sc.take((size_t)NHEAD * nx * sizeof(real)) : head0;
     real *buf0 = (real *)sc.take((size_t)CH * nx * sizeof(real));
-    real *buf1 = (real *)sc.take((size_t)CH * nx * sizeof(real));
+    // nbuf = 2: chunk j + 2 prefetched while chunk j + 1 runs; nbuf = 1: one
+    // chunk buffer, for two blocks per SM
+    real *buf1 = nbuf > 1 ? (real *)sc.take((size_t)CH * nx * sizeof(real)) : buf0;
     C *wk = (C *)sc.take((size_t)max(CH, 3) * ph * sizeof(C));
     const Lay la{h, 1, 0}, lb{ph, 1, 1};
     const int nchunk = (NMOV + CH - 1) / CH;
@@ -782,10 +784,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, h);
         if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, h);
         if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, nchunk, CH, nx, ny, slot, h);
-        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, nchunk, CH, nx, ny, slot, h);
+        if (nbuf > 1 && njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, nchunk, CH, nx, ny, slot, h);
     }
     uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
-    bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
+    bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
     const real dt = P.dt, itau = real(1) / P.tau;
     const bool with_base = alpha != real(0);
     for (int j = 0; j < njobs; ++j) {
@@ -923,9 +925,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
-            if (j + 2 < njobs) {
-                k5_issue_chunk<real>(spec, B, odd ? &bar1 : &bar0, j + 2, nchunk, CH, nx, ny, slot, h);
-                if (odd) pend1 = true;
+            if (j + nbuf < njobs) {
+                const bool nodd = (j + nbuf) & 1;   // the barrier of chunk j + nbuf
+                k5_issue_chunk<real>(spec, B, nodd ? &bar1 : &bar0, j + nbuf, nchunk, CH, nx, ny, slot, h);
+                if (nodd) pend1 = true;
                 else pend0 = true;
             }
             // the row's head buffer is free after its last chunk: prefetch
