@@ -86,7 +86,7 @@ def ncu_traffic(kernel, precision, n):
 _UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024.0, "MB": 1024.0 ** 2, "GB": 1024.0 ** 3}
 
 
-def write_ncu_traffic(csv_path, precision, n, note):
+def write_ncu_traffic(csv_path, precision, n, note, out_path=None):
     """Writes profiles/ncu_traffic.txt from an ncu --csv log of one SSP-RK3
     step of the pipelined kernels captured with the metrics
     dram__bytes_read.sum and dram__bytes_write.sum: DRAM bytes per launch of
@@ -118,7 +118,7 @@ def write_ncu_traffic(csv_path, precision, n, note):
         else:
             continue
         out.setdefault(k, []).append(by)
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    path = out_path or os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     with open(path, "w") as fh:
         fh.write("# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), averaged over the\n"
                  "# launches of one SSP-RK3 step; valid for the kernel sources with this hash only.\n"

@@ -57,3 +57,35 @@ def test_reference_arm_does_no_work_on_other_ranks(capsys):
     args = argparse.Namespace(steps=3, warmup=3, grid=1024)
     assert bench.run_reference(args, rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_ncu_traffic_summary_from_a_launch_csv(tmp_path):
+    """bench.write_ncu_traffic: DRAM read + write per launch, unit-scaled,
+    averaged per kernel kind; the two multi-group column launches of a stage
+    alternate between level 1 and level 2."""
+    sys.path.insert(0, ROOT)
+    import bench
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
+          '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    names = ["void k1_pipe<float, 4>(x)", "void kcol_pipe<float, 0>(x)", "void kcol_pipe<float, 1>(x)",
+             "void k3_pipe<float>(x)", "void kcol_pipe<float, 1>(x)", "void k5_pipe<float, 2>(x)"]
+    lines = ["==PROF== noise\n", hdr]
+    for stage in range(2):
+        for j, nm in enumerate(names):
+            i = 6 * stage + j
+            rd, wr = 1000.0 * (j + 1) + stage, 10.0 * (j + 1)
+            for metric, unit, val in (("dram__bytes_read.sum", "Kbyte", rd / 1e3), ("dram__bytes_write.sum", "byte", wr),
+                                      ("gpu__time_duration.sum", "ns", 5.0)):
+                lines.append(f'"{i}","1","python","h","{nm}","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","s",'
+                             f'"{metric}","{unit}","{val}"\n')
+    csv_path = tmp_path / "t.csv"
+    csv_path.write_text("".join(lines))
+    out = tmp_path / "traffic.txt"
+    res = bench.write_ncu_traffic(str(csv_path), 32, 1024, "test", out_path=str(out))
+    want = {"row_forward_moments": 1, "col_convection": 2, "col_level1": 3, "row_level1": 4, "col_level2": 5,
+            "row_final": 6}
+    for k, j in want.items():
+        assert len(res[k]) == 2
+        assert sum(res[k]) / 2 == pytest.approx(1000.0 * j + 0.5 + 10.0 * j)
+    rows = [ln.split() for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    assert {r[0] for r in rows} == set(want) and all(r[1] == "32" and r[2] == "1024" for r in rows)
