@@ -2,16 +2,21 @@
 // described at the top of engine_impl.cuh).  Every kernel stages its global
 // inputs into shared memory with asynchronous bulk / tensor copies
 // (async_copy.cuh) so that the HBM traffic of the next job overlaps the
-// transforms of the current one, and transforms out of place between the
-// staged (unpadded) buffer and a padded work buffer (pp_fft):
+// transforms of the current one (within a block when it holds two staging
+// buffers, across the blocks of an SM when it holds one), and transforms
+// out of place between the staged (unpadded) buffer and a padded work
+// buffer (pp_fft).  The job lists run over the rows or column tiles of all
+// runs of a batch (KP::nrun):
 //   k1_pipe    persistent over rows; chunks of CH distribution rows,
 //              double-buffered; moments accumulate in registers.
-//   kcol_pipe  persistent over (group, column tile) jobs; TW-wide column
-//              tiles fetched by 2-D tensor copies, double-buffered.
+//   kcol_pipe  persistent over (run, group, column tile) jobs; TW-wide
+//              column tiles fetched by 2-D tensor copies into one or two
+//              buffers; the spectral multiply is fused with the last
+//              forward pass and its adjoint (fft_device.cuh).
 //   k3_pipe    one row per block: 15 derivative rows + rho, T.
 //   k5_pipe    persistent over rows; the per-row head (level-2 spectra,
 //              fields, aux) and CH-row chunks of convection spectra are
-//              prefetched.
+//              prefetched (one or two chunk buffers).
 #pragma once
 
 #include "async_copy.cuh"
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
 }
 
 // ---------------------------------------------------------------------------
-// Column pass (persistent over (group, tile) jobs, double-buffered)
+// Column pass (persistent over (run, group, tile) jobs, one or two tile buffers)
 // ---------------------------------------------------------------------------
 
 template <typename real>
