@@ -58,12 +58,19 @@ def measured_peaks():
 
 
 def source_hash():
+    """Hash of the kernel sources' code: every file of csrc/ without its
+    whole-line // comments and blank lines, so that a comment edit does not
+    detach the ncu traffic figures from the kernels they were taken on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1011_3582_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
-            h.update(fh.read())
+            for line in fh.read().decode("utf-8", "replace").splitlines():
+                t = line.strip()
+                if t and not t.startswith("//"):
+                    h.update(t.encode())
+                    h.update(b"\n")
     return h.hexdigest()[:16]
 
 
