@@ -68,9 +68,25 @@ def _compile(src, extra):
 
 
 def build(force=False, verbose=False, extra=()):
+    """Build if needed.  Concurrent callers (one process per GPU under
+    torch.distributed.run, parallel test workers) are serialised by an
+    exclusive lock on _build/.lock: the first builds, the others then find
+    the library up to date."""
     if not force and up_to_date(extra):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date(extra):
+                return LIB
+            return _build_locked(verbose, extra)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra):
     extra = list(extra) + env_flags()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), sources()))
