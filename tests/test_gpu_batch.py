@@ -49,8 +49,12 @@ def test_batch_matches_single_handles(fl):
         assert inv[r]["time"] == pytest.approx(7e-5)
 
 
-def test_autotune_keeps_results_and_state(fl):
+@pytest.mark.parametrize("integrator", [3, 1])
+def test_autotune_keeps_results_and_state(fl, integrator):
+    """For SSP-RK3 the candidates write the stage buffer, for Euler a
+    temporary one: the state is never touched."""
     fields, kw = slab_case(64, 0.9, 32, 5)
+    kw = dict(kw, integrator=integrator)
     with fl.Handle(fl.params(**kw)) as h:
         h.set_fields(*fields)
         f0 = h.get_f()
@@ -73,3 +77,23 @@ def test_batch_rejects_bad_arguments(fl):
         fl.Batch([])
     with pytest.raises(fl.FFTLBError):
         fl.Batch([fl.params(nx=10, ny=16)])
+
+
+def test_batch_of_euler_runs_matches_single_handles(fl):
+    """Two Euler runs of one grid share one batched engine (no RK stage
+    buffer; autotune times into a temporary buffer)."""
+    cases = [slab_case(64, 0.9, 64, 8), slab_case(64, 0.8, 64, 9)]
+    for _, kw in cases:
+        kw["integrator"] = 1
+    with fl.Batch([fl.params(**kw) for _, kw in cases], autotune=True) as b:
+        for r, (fields, _) in enumerate(cases):
+            b.set_fields(r, *fields)
+        b.step(5)
+        got = [b.get_f(r) for r in range(2)]
+        tun = [b.tuning(r) for r in range(2)]
+    for r, (fields, kw) in enumerate(cases):
+        with fl.Handle(fl.params(**kw)) as h:
+            h.tuning(tun[r])
+            h.set_fields(*fields)
+            h.step(5)
+            assert np.array_equal(got[r], h.get_f()), r
