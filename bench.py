@@ -21,6 +21,7 @@ for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
 import argparse
 import hashlib
 import json
+import re
 import statistics
 import subprocess
 import sys
@@ -117,7 +118,8 @@ def write_ncu_traffic(csv_path, precision, n, note, out_path=None):
         elif "k5_pipe" in name:
             k = "row_final"
         elif "kcol_pipe" in name:
-            if "false" in name or ", 0>" in name:
+            m = re.search(r"kcol_pipe<\s*\w+\s*,\s*(\w+)", name)   # the second template argument: MULTI
+            if m and m.group(1) in ("false", "0"):
                 k = "col_convection"
             else:
                 k = "col_level1" if multi % 2 == 0 else "col_level2"
@@ -292,6 +294,10 @@ def main():
                     help="write profiles/ncu_traffic.txt from an ncu --csv log of one step (no GPU work)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch parameters instead of fftlb_autotune's")
+    ap.add_argument("--bf16split", action="store_true",
+                    help="time the fp32 path with split-BF16 tensor-core first passes as the main path (profiling)")
+    ap.add_argument("--no-bf16split", action="store_true",
+                    help="skip the FP32 path with split-BF16 tensor-core first radix-16 passes")
     ap.add_argument("--no-cufft-reference", action="store_true",
                     help="skip timing the PyTorch/cuFFT version of the same step")
     ap.add_argument("--no-sweep", action="store_true",
@@ -363,7 +369,8 @@ def main():
         return ms, prof, inv, lps, (clk.summary(t0, t1, busy0, busy1) if sample_clocks else None)
 
     tuned = {}
-    ms, prof, inv, lps, clocks = time_path(args.precision, args.steps, args.warmup, True)
+    prec = args.precision | (256 if args.bf16split and args.precision == 32 else 0)   # 256: BF16SPLIT
+    ms, prof, inv, lps, clocks = time_path(prec, args.steps, args.warmup, True)
     K = args.steps
     value = rep.throughput(n * n * K, ms * 1e-3) / 1e6
 
@@ -371,7 +378,7 @@ def main():
     top = max(prof, key=lambda k: prof[k][0])
     tms, tl, tbytes = prof[top]
     achieved = tbytes / (tms * 1e-3 / tl) / 1e9
-    traffic = ncu_traffic(top, args.precision, n)
+    traffic = ncu_traffic(top, prec, n)
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind,
                 "kernel_share": tms / sum(v[0] for v in prof.values())}
@@ -387,6 +394,16 @@ def main():
         fp64 = {"value": world * n * n * max(2, K // 4) / (ms64 * 1e-3) / 1e6, "unit": "MLUPS",
                 "ms_per_step": ms64 / max(2, K // 4)}
 
+    bf16split = None
+    if not args.no_bf16split and prec == 32:
+        ks = max(2, K // 2)
+        pb = 32 | fftlb.BF16SPLIT
+        mss, profs, _, _, _ = time_path(pb, ks, 3, False)
+        bf16split = {"value": world * n * n * ks / (mss * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": mss / ks,
+                     "kernel_ms_per_launch": {k: profs[k][0] / max(profs[k][1], 1) for k in profs},
+                     "what": "fp32 with the first radix-16 pass of every power-of-two transform as a split-BF16 "
+                             "DFT matrix product on the tensor cores (mma.sync m16n8k16, fp32 accumulation)"}
+
     e2e = None
     if not args.no_e2e:
         # public API with pinned host buffers: upload the fields, then each
@@ -396,10 +413,10 @@ def main():
         for dst, src in zip(pinned, fields):
             dst[...] = src
         outs = [torch.empty((n, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
-        h = fftlb.Handle(workload_params(fftlb, n, args.precision), stream=stream.cuda_stream)
+        h = fftlb.Handle(workload_params(fftlb, n, prec), stream=stream.cuda_stream)
         h.set_fields(*pinned)
         if not args.no_autotune:
-            h.tuning(tuned[args.precision])   # the parameters the timed run used
+            h.tuning(tuned[prec])   # the parameters the timed run used
         h.step(2)
         torch.cuda.synchronize()
         barrier()
@@ -423,7 +440,7 @@ def main():
         plist, flist = [], []
         for r_, (n_, tr) in enumerate(plan):
             flist.append(workloads.spinodal(n_, n_, RHOC, tr * TC, amp=0.01, seed=100 + r_))
-            plist.append(fftlb.params(nx=n_, ny=n_, a=A, b=B, precision=args.precision, integrator=3, window=4))
+            plist.append(fftlb.params(nx=n_, ny=n_, a=A, b=B, precision=prec, integrator=3, window=4))
         t0 = time.perf_counter()
         bt = fftlb.Batch(plist, autotune=True, stream=stream.cuda_stream)
         t_create = time.perf_counter() - t0
@@ -487,12 +504,13 @@ def main():
                            "l2": "inputs larger than L2 (state %.0f MB + spectra %.0f MB)" % (
                                33 * n * n * args.precision / 8 / 1e6, 58 * n * n * args.precision / 8 / 1e6),
                            "parallelism": "replicas" if world > 1 else "single",
+                           "first_pass": "split-BF16 tensor cores" if prec & 256 else "fp32 radix 16",
                            "launch_tuning": dict(zip(("tw_conv", "tw_level", "rows_forward", "rows_final",
-                                                      "head_buffers"), tuned[args.precision]),
+                                                      "head_buffers"), tuned[prec]),
                                                  autotuned=not args.no_autotune)},
                 "roofline": roofline, "kernels": kernels, "alg_bytes_per_step": step_bytes,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
-                "fp64": fp64, "sweep": sweep, "cufft_reference": cufft, "invariants_after": inv}
+                "fp64": fp64, "bf16split": bf16split, "sweep": sweep, "cufft_reference": cufft, "invariants_after": inv}
         print(json.dumps(line), flush=True)
     rep.close()
 

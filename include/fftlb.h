@@ -61,10 +61,17 @@ typedef enum {
  *  window      0 = exact k; 1..4 = k_1..k_4 of Eqs. K1-K4 [4]
  *  integrator  1 = forward Euler, 3 = SSP-RK3 (Shu-Osher)
  *  precision   64 = everything in fp64; 32 = FFTs and pointwise in fp32
- *              (conservation sums still fp64)
+ *              (conservation sums still fp64); 32 | FFTLB_BF16SPLIT = fp32
+ *              with the first radix-16 pass of every power-of-two row and
+ *              column transform computed on the tensor cores as a DFT
+ *              matrix product, operands split into bfloat16 hi + lo parts,
+ *              fp32 accumulation (about 2^-16 relative error in that pass
+ *              against 2^-24 in fp32; other lengths unchanged)
  *  check_every fftlb_step checks the state for non-finite or unphysical
  *              values every check_every steps (0 = never)
  */
+#define FFTLB_BF16SPLIT 256
+
 typedef struct {
     int nx, ny;
     double dx, dt, tau, a, b, K, H, q, zeta;

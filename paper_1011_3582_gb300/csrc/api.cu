@@ -56,11 +56,12 @@ fftlb_status fftlb_create(fftlb_t *h, const fftlb_params *p, const fftlb_velset 
         if (vs->speeds)
             for (int i = 0; i < 4; ++i) speeds[i] = vs->speeds[i];
     }
-    if (p->precision != 64 && p->precision != 32)
-        return fail(nullptr, FFTLB_ERR_ARG, "precision must be 64 or 32");
+    if (p->precision != 64 && p->precision != 32 && p->precision != (32 | FFTLB_BF16SPLIT))
+        return fail(nullptr, FFTLB_ERR_ARG, "precision must be 64, 32 or 32 | FFTLB_BF16SPLIT");
     fftlb_t hh = new (std::nothrow) fftlb_s();
     if (!hh) return fail(nullptr, FFTLB_ERR_OOM, "host allocation failed");
-    hh->eng = p->precision == 64 ? fftlb::make_engine_f64() : fftlb::make_engine_f32();
+    hh->eng = p->precision == 64 ? fftlb::make_engine_f64()
+              : p->precision == 32 ? fftlb::make_engine_f32() : fftlb::make_engine_f32_split();
     fftlb::Status st = hh->eng->init(*p, speeds, reinterpret_cast<cudaStream_t>(stream), 1);
     if (!st.good()) {
         delete hh->eng;

@@ -100,8 +100,9 @@ fftlb_status fftlb_batch_create(fftlb_batch_t *out, int nruns, const fftlb_param
             for (int i = 0; i < 4; ++i) speeds[i] = vs->speeds[i];
     }
     for (int r = 0; r < nruns; ++r)
-        if (params[r].precision != 64 && params[r].precision != 32)
-            return fail(nullptr, FFTLB_ERR_ARG, "run " + std::to_string(r) + ": precision must be 64 or 32");
+        if (params[r].precision != 64 && params[r].precision != 32 && params[r].precision != (32 | FFTLB_BF16SPLIT))
+            return fail(nullptr, FFTLB_ERR_ARG,
+                        "run " + std::to_string(r) + ": precision must be 64, 32 or 32 | FFTLB_BF16SPLIT");
     fftlb_batch_t b = new (std::nothrow) fftlb_batch_s();
     if (!b) return fail(nullptr, FFTLB_ERR_OOM, "host allocation failed");
     b->user = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -130,7 +131,8 @@ fftlb_status fftlb_batch_create(fftlb_batch_t *out, int nruns, const fftlb_param
         const std::vector<int> &runs = groups[order[gi]];
         fftlb_params p = params[runs[0]];
         p.check_every = 0;
-        fftlb::Engine *eng = p.precision == 64 ? fftlb::make_engine_f64() : fftlb::make_engine_f32();
+        fftlb::Engine *eng = p.precision == 64 ? fftlb::make_engine_f64()
+                             : p.precision == 32 ? fftlb::make_engine_f32() : fftlb::make_engine_f32_split();
         b->eng.push_back(eng);
         fftlb::Status st = eng->init(p, speeds, b->origin, (int)runs.size());
         if (!st.good()) return bad(st.code, "run " + std::to_string(runs[0]) + ": " + st.msg);

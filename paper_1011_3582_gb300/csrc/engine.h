@@ -76,6 +76,7 @@ extern const char *const kKernelNames[KK_COUNT];
 
 Engine *make_engine_f64();
 Engine *make_engine_f32();
+Engine *make_engine_f32_split();   // precision 32 | FFTLB_BF16SPLIT
 
 // the engine behind a handle (NULL for a NULL handle); defined in api.cu
 Engine *engine_of(fftlb_t h);

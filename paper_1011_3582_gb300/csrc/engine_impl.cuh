@@ -82,9 +82,12 @@ template <> __device__ __forceinline__ float FKC<float>(int k, int j) { return c
 // spectra [run][58][ny][nx/2], fields [run][4][ny][nx], aux [run][3][ny][nx]);
 // the pipelined kernels treat the nrun * ny rows (or column tiles) of all
 // runs as one job list
+// tc16: the A fragments of the split-BF16 tensor-core first pass
+// (tc_dft16_pass), or nullptr for the plain radix-16 first pass
 template <typename real> struct KP {
     int nx, ny, h, nrun;
     real dx, dt, tau, a, b, K, H, q, zeta, scale;
+    const uint4 *tc16;
 };
 
 // One column-pass group: up to 2 input spectra and 6 outputs; every output
@@ -453,7 +456,10 @@ static inline bool valid_len(int n) {
     return n == 1;
 }
 
-template <typename real>
+// SPLIT: fp32 with the split-BF16 tensor-core first radix-16 passes (the
+// kernels' TC instantiations; a separate engine type so that the plain
+// kernels carry none of that code)
+template <typename real, bool SPLIT = false>
 class EngineT : public Engine {
     using C = typename cplx_of<real>::type;
 
@@ -637,6 +643,8 @@ class EngineT : public Engine {
     C *Wr_ = nullptr, *Wp_ = nullptr, *Wc_ = nullptr;
     C *Tr_ = nullptr, *Tc_ = nullptr;   // pass twiddle tables (power-of-two lengths), radix 16 first
     C *Tr8_ = nullptr;                  // rows, radix 8 first
+    static constexpr bool split_ = SPLIT && sizeof(real) == 4;   // split-BF16 tensor-core first passes
+    uint4 *tc16_ = nullptr;             // their A fragments (dft16_fragments)
     int ntr_ = 0, ntc_ = 0, ntr8_ = 0;
     GroupDesc *groups_ = nullptr;
     double *partial_ = nullptr, *red_ = nullptr;
@@ -934,7 +942,58 @@ class EngineT : public Engine {
         if (ntr_) FFTLB_CU(cudaMemcpy(Tr_, tr.data(), tr.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntr8_) FFTLB_CU(cudaMemcpy(Tr8_, tr8.data(), tr8.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntc_) FFTLB_CU(cudaMemcpy(Tc_, tc.data(), tc.size() * sizeof(C), cudaMemcpyHostToDevice));
+        if (split_) {
+            std::vector<uint4> fr;
+            dft16_fragments(fr);
+            if (!(st = dalloc(&tc16_, fr.size())).good()) return st;
+            FFTLB_CU(cudaMemcpy(tc16_, fr.data(), fr.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+        }
         return Status::ok();
+    }
+
+    // bfloat16 nearest-even of a double (through float: the lo part of the
+    // split absorbs any double rounding) and its value
+    static uint16_t bf16_rne(double v) {
+        const float f = (float)v;
+        uint32_t u;
+        memcpy(&u, &f, 4);
+        u += 0x7fffu + ((u >> 16) & 1u);
+        return (uint16_t)(u >> 16);
+    }
+    static double bf16_value(uint16_t b) {
+        const uint32_t u = (uint32_t)b << 16;
+        float f;
+        memcpy(&f, &u, 4);
+        return f;
+    }
+
+    // A fragments of the forward 16-point DFT matrix for tc_dft16_pass: for
+    // lane (g, q) = (lane / 4, lane % 4), uint4 (a0, a1, a2, a3) of Wr_hi,
+    // Wr_lo, Wi_hi, Wi_lo, with Wr = cos(2 pi m k / 16), Wi = -sin(...);
+    // register r covers row m = g + 8 (r & 1) and columns k0, k0 + 1 with
+    // k0 = 2q + 8 (r >> 1), column k0 in the lower half
+    static void dft16_fragments(std::vector<uint4> &fr) {
+        fr.assign(128, uint4{0, 0, 0, 0});
+        for (int lane = 0; lane < 32; ++lane) {
+            const int g = lane >> 2, q = lane & 3;
+            for (int part = 0; part < 4; ++part) {
+                uint32_t r[4];
+                for (int reg = 0; reg < 4; ++reg) {
+                    const int m = g + 8 * (reg & 1), k0 = 2 * q + 8 * (reg >> 1);
+                    uint32_t packed = 0;
+                    for (int hlf = 0; hlf < 2; ++hlf) {
+                        const double ang = 2.0 * M_PI * ((m * (k0 + hlf)) % 16) / 16.0;
+                        double w = part < 2 ? std::cos(ang) : -std::sin(ang);
+                        if (std::fabs(w) < 1e-12) w = 0.0;
+                        const uint16_t hi = bf16_rne(w);
+                        const uint16_t v = (part & 1) ? bf16_rne(w - bf16_value(hi)) : hi;
+                        packed |= (uint32_t)v << (16 * hlf);
+                    }
+                    r[reg] = packed;
+                }
+                fr[4 * lane + part] = uint4{r[0], r[1], r[2], r[3]};
+            }
+        }
     }
 
     static GroupDesc group(int nin, int in0, int in1) {
@@ -1076,6 +1135,7 @@ class EngineT : public Engine {
         kp_.q = (real)p_.q;
         kp_.zeta = (real)p_.zeta;
         kp_.scale = (real)(1.0 / ((double)nx_ * (double)ny_));
+        kp_.tc16 = split_ ? tc16_ : nullptr;
         return configure_pipe(budget);
     }
 
@@ -1147,7 +1207,7 @@ class EngineT : public Engine {
             const size_t s = col_smem(multi, tw, nb2);
             if (s > budget_) continue;
             int nb = 0;
-            Status st = multi ? occupancy(kcol_pipe<real, true>, NTC, s, &nb) : occupancy(kcol_pipe<real, false>, NTC, s, &nb);
+            Status st = multi ? occupancy(kcol_pipe<real, true, SPLIT>, NTC, s, &nb) : occupancy(kcol_pipe<real, false, SPLIT>, NTC, s, &nb);
             if (!st.good()) return st;
             if (nb > best) {
                 best = nb;
@@ -1161,7 +1221,9 @@ class EngineT : public Engine {
     }
     // largest row radix for a kernel transforming `rows` rows at a time with
     // nthr threads: radix 16 unless its passes would leave threads idle
-    int row_maxlr(int rows, int nthr) const { return rows * (h_ / 16) < nthr ? 3 : 4; }
+    // radix-8-first rows when radix-16 passes would leave threads idle (the
+    // split-BF16 mode keeps radix 16 first: its first pass is the DFT product)
+    int row_maxlr(int rows, int nthr) const { return !split_ && rows * (h_ / 16) < nthr ? 3 : 4; }
     static int smax_for(int nx, int nt, int cap) {
         const int s = (nx + nt - 1) / nt;
         int r = 1;
@@ -1170,17 +1232,17 @@ class EngineT : public Engine {
     }
     Status occ_k1(size_t sm, int *nb) {
         switch (SMAX1_) {
-        case 1: return occupancy(k1_pipe<real, 1>, NT1, sm, nb);
-        case 2: return occupancy(k1_pipe<real, 2>, NT1, sm, nb);
-        case 4: return occupancy(k1_pipe<real, 4>, NT1, sm, nb);
-        default: return occupancy(k1_pipe<real, 8>, NT1, sm, nb);
+        case 1: return occupancy(k1_pipe<real, 1, SPLIT>, NT1, sm, nb);
+        case 2: return occupancy(k1_pipe<real, 2, SPLIT>, NT1, sm, nb);
+        case 4: return occupancy(k1_pipe<real, 4, SPLIT>, NT1, sm, nb);
+        default: return occupancy(k1_pipe<real, 8, SPLIT>, NT1, sm, nb);
         }
     }
     Status occ_k5(size_t sm, int *nb) {
         switch (SMAX5_) {
-        case 1: return occupancy(k5_pipe<real, 1>, NT5, sm, nb);
-        case 2: return occupancy(k5_pipe<real, 2>, NT5, sm, nb);
-        default: return occupancy(k5_pipe<real, 4>, NT5, sm, nb);
+        case 1: return occupancy(k5_pipe<real, 1, SPLIT>, NT5, sm, nb);
+        case 2: return occupancy(k5_pipe<real, 2, SPLIT>, NT5, sm, nb);
+        default: return occupancy(k5_pipe<real, 4, SPLIT>, NT5, sm, nb);
         }
     }
 
@@ -1240,8 +1302,8 @@ class EngineT : public Engine {
                     int nb = 0;
                     const size_t sm = col_smem(multi, tw, nbuf);
                     if (sm > budget) continue;
-                    Status s2 = multi ? occupancy(kcol_pipe<real, true>, NTC, sm, &nb)
-                                      : occupancy(kcol_pipe<real, false>, NTC, sm, &nb);
+                    Status s2 = multi ? occupancy(kcol_pipe<real, true, SPLIT>, NTC, sm, &nb)
+                                      : occupancy(kcol_pipe<real, false, SPLIT>, NTC, sm, &nb);
                     if (!s2.good()) return s2;
                     // most blocks per SM, then the widest tile, then two buffers
                     const int score = nb * 1000 + tw * 10 + nbuf;
@@ -1271,7 +1333,7 @@ class EngineT : public Engine {
                 const size_t sm = smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, (size_t)ND1 * h_ * cs, (size_t)wr * ph * cs,
                                               (size_t)2 * nx_ * rs});
                 if (sm > budget) continue;
-                if (!(st = occupancy(k3_pipe<real>, NT3, sm, &nb)).good()) return st;
+                if (!(st = occupancy(k3_pipe<real, SPLIT>, NT3, sm, &nb)).good()) return st;
                 if (nb > bestnb) {
                     bestnb = nb;
                     WR3_ = wr;
@@ -1471,11 +1533,11 @@ class EngineT : public Engine {
   private:
     Status launch_col(int first, int count, bool level1) {
         if (level1)
-            kcol_pipe<real, true><<<gridl_, NTC, smeml_, stream_>>>(specb_, groups_ + first, count, kxt_,
+            kcol_pipe<real, true, SPLIT><<<gridl_, NTC, smeml_, stream_>>>(specb_, groups_ + first, count, kxt_,
                                                                                kyt_, Wc_, Tc_, ntc_, kp_, TWl_, BOXR_,
                                                                                NBUFl_, tmap_l1_, err_);
         else
-            kcol_pipe<real, false><<<gridc_, NTC, smemc_, stream_>>>(
+            kcol_pipe<real, false, SPLIT><<<gridc_, NTC, smemc_, stream_>>>(
                 specb_, groups_ + first, count, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWc_, BOXR_, NBUFc_, tmap_conv_, err_);
         FFTLB_LAUNCHED("kcol_pipe");
         return Status::ok();
@@ -1485,15 +1547,15 @@ class EngineT : public Engine {
         Status st;
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
         if (SMAX1_ == 1)
-            k1_pipe<real, 1><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 1, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 2)
-            k1_pipe<real, 2><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 2, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 4)
-            k1_pipe<real, 4><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
+            k1_pipe<real, 4, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
         else
-            k1_pipe<real, 8><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
+            k1_pipe<real, 8, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
         FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
@@ -1505,7 +1567,7 @@ class EngineT : public Engine {
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
         {
             const int ml = row_maxlr(WR3_, NT3);
-            k3_pipe<real><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, ml == 3 ? Tr8_ : Tr_,
+            k3_pipe<real, SPLIT><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, ml == 3 ? Tr8_ : Tr_,
                                                               ml == 3 ? ntr8_ : ntr_, kp_, WR3_, ml, err_);
         }
         FFTLB_LAUNCHED("k3_pipe");
@@ -1516,13 +1578,13 @@ class EngineT : public Engine {
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         const int ml5 = row_maxlr(CH5_, NT5);
         if (SMAX5_ == 1)
-            k5_pipe<real, 1><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 1, SPLIT><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, NBUF5_, ml5, err_);
         else if (SMAX5_ == 2)
-            k5_pipe<real, 2><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 2, SPLIT><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, NBUF5_, ml5, err_);
         else
-            k5_pipe<real, 4><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
+            k5_pipe<real, 4, SPLIT><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,
                                                                Wp_, ml5 == 3 ? Tr8_ : Tr_, ml5 == 3 ? ntr8_ : ntr_, kp_, CH5_, NHB5_, NBUF5_, ml5, err_);
         FFTLB_LAUNCHED("k5_pipe");
         return prof_end();

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace fftlb {
 
 template <typename real> struct cplx_of;
@@ -304,6 +306,150 @@ __device__ __forceinline__ void pp_pass_p2(const C *src, int sbs, int ses, C *ds
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split-BF16 tensor-core first pass (fp32 transforms in the BF16SPLIT mode).
+// The first radix-16 pass of a power-of-two Stockham transform has no
+// twiddles: every butterfly is a 16-point DFT, so the pass is the product
+// Y = W X of the DFT matrix W (W[m][t] = exp(DIR 2 pi i m t / 16)) with the
+// 16 x nbutterfly matrix X of the butterflies' inputs.  Over the reals,
+//   [Re Y]   [ Wr  -Wi ] [Re X]
+//   [Im Y] = [ Wi   Wr ] [Im X],
+// which for 8 butterflies is two m16n8k16 row tiles (Re Y, Im Y) times two
+// k16 steps (Re X, Im X).  Every real operand z is split into bfloat16
+// z_hi = bf16(z) and z_lo = bf16(z - z_hi) (round to nearest even); the
+// product keeps W_hi X_hi + W_hi X_lo + W_lo X_hi, accumulated in fp32 by
+// mma.sync (the dropped W_lo X_lo and the rounding of z_lo are each below
+// 2^-16 of |W| |X|).  A warp takes 8 butterflies at a time; lane (g, q) =
+// (lane / 4, lane % 4) loads inputs t = 2q, 2q+1, 2q+8, 2q+9 of butterfly g
+// (the B fragment) and stores outputs m = g, g+8 of butterflies 2q, 2q+1
+// (the accumulator fragment).
+//
+// frag: per lane, the A fragments of Wr_hi, Wr_lo, Wi_hi, Wi_lo of the
+// forward direction (Wi = -sin), 4 uint4 (a0..a3: rows g / g+8, columns
+// 2q, 2q+1 / 2q+8, 2q+9; the lower column in the lower half).
+// ADJ = false: reads e = jj + t n/16, writes jj 16 + m (the pass P_1 of
+// pp_pass_p2); ADJ = true: reads jj 16 + t, writes jj + m n/16 (its adjoint,
+// pp_pass_p2_adj at Ns = 1, with DIR = +1).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t bf16x2_rn(float first, float second) {
+    uint32_t d;   // first in the lower half
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(second), "f"(first));
+    return d;
+}
+
+// hi / lo bfloat16 split of two floats (packed like bf16x2_rn)
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    hi = bf16x2_rn(a, b);
+    lo = bf16x2_rn(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint4 &a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint4 bf16x2_neg(uint4 a) {
+    const uint32_t s = 0x80008000u;
+    return uint4{a.x ^ s, a.y ^ s, a.z ^ s, a.w ^ s};
+}
+
+template <int DIR, bool BFAST, bool ADJ, int PADS, int PADD>
+__device__ __forceinline__ void tc_dft16_pass(const float2 *src, int sbs, int ses, float2 *dst, int dbs, int des,
+                                              int logn, int nbatch, int lognbatch, const uint4 *frag, int tid,
+                                              int nthr) {
+    const int lognb = logn - 4;
+    const int nb = 1 << lognb;
+    const int total = nbatch << lognb;
+    const int lane = tid & 31, g = lane >> 2, q = lane & 3;
+    const uint4 *fl = frag + 4 * lane;
+    const uint4 wr_hi = fl[0], wr_lo = fl[1];
+    const uint4 wi_hi = DIR < 0 ? fl[2] : bf16x2_neg(fl[2]);
+    const uint4 wi_lo = DIR < 0 ? fl[3] : bf16x2_neg(fl[3]);
+    const uint4 nwi_hi = bf16x2_neg(wi_hi), nwi_lo = bf16x2_neg(wi_lo);
+    for (int J0 = (tid >> 5) * 8; J0 < total; J0 += (nthr >> 5) * 8) {   // warp-uniform
+        const int J = J0 + g;
+        const bool ok = J < total;
+        const int Jc = ok ? J : 0;
+        int b, jj;
+        if (BFAST) {
+            b = Jc & (nbatch - 1);
+            jj = Jc >> lognbatch;
+        } else {
+            b = Jc >> lognb;
+            jj = Jc & (nb - 1);
+        }
+        float2 x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int t = 2 * q + (i & 1) + (i >> 1) * 8;
+            const int e = ADJ ? (jj << 4) + t : jj + t * nb;
+            const float2 v = src[b * sbs + (PADS ? e + (e >> 4) : e) * ses];
+            x[i] = ok ? v : float2{0.f, 0.f};
+        }
+        uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
+        split_bf16x2(x[0].x, x[1].x, rh0, rl0);   // Re X rows 2q, 2q+1
+        split_bf16x2(x[2].x, x[3].x, rh1, rl1);   // Re X rows 2q+8, 2q+9
+        split_bf16x2(x[0].y, x[1].y, ih0, il0);
+        split_bf16x2(x[2].y, x[3].y, ih1, il1);
+        float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
+        __syncwarp();
+        // Re Y = Wr Re X - Wi Im X (small terms first)
+        mma_bf16_16816(yr, wr_lo, rh0, rh1);
+        mma_bf16_16816(yr, nwi_lo, ih0, ih1);
+        mma_bf16_16816(yr, wr_hi, rl0, rl1);
+        mma_bf16_16816(yr, nwi_hi, il0, il1);
+        mma_bf16_16816(yr, wr_hi, rh0, rh1);
+        mma_bf16_16816(yr, nwi_hi, ih0, ih1);
+        // Im Y = Wi Re X + Wr Im X
+        mma_bf16_16816(yi, wi_lo, rh0, rh1);
+        mma_bf16_16816(yi, wr_lo, ih0, ih1);
+        mma_bf16_16816(yi, wi_hi, rl0, rl1);
+        mma_bf16_16816(yi, wr_hi, il0, il1);
+        mma_bf16_16816(yi, wi_hi, rh0, rh1);
+        mma_bf16_16816(yi, wr_hi, ih0, ih1);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int Jo = J0 + 2 * q + c;
+            if (Jo < total) {
+                int bo, jo;
+                if (BFAST) {
+                    bo = Jo & (nbatch - 1);
+                    jo = Jo >> lognbatch;
+                } else {
+                    bo = Jo >> lognb;
+                    jo = Jo & (nb - 1);
+                }
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int m = g + 8 * hh;
+                    const int e = ADJ ? jo + m * nb : (jo << 4) + m;
+                    dst[bo * dbs + (PADD ? e + (e >> 4) : e) * des] = float2{yr[c + 2 * hh], yi[c + 2 * hh]};
+                }
+            }
+        }
+    }
+}
+
+// the first pass through tc_dft16_pass when it applies (fp32, radix 16,
+// Ns = 1, a fragment table given); returns false otherwise
+template <int DIR, bool BFAST, bool ADJ, int PADS, int PADD, typename C>
+__device__ __forceinline__ bool tc_first_pass(int lr, int logNs, const C *src, int sbs, int ses, C *dst, int dbs,
+                                              int des, int logn, int nbatch, int lognbatch, const uint4 *tc, int tid,
+                                              int nthr) {
+    if constexpr (std::is_same<C, float2>::value) {
+        if (tc != nullptr && lr == 4 && logNs == 0) {
+            tc_dft16_pass<DIR, BFAST, ADJ, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, tc,
+                                                       tid, nthr);
+            return true;
+        }
+    }
+    return false;
+}
+
 // Per-pass twiddle tables of a power-of-two length n for the radix plan of
 // pp_fft_p2 with largest radix 2^maxlr (2^maxlr while at least maxlr bits
 // remain, then the rest): for every pass with Ns > 1, Ns * R entries
@@ -328,13 +474,17 @@ __host__ __device__ inline int pass_twiddle_len(int n, int maxlr = 4) {
 // for batches whose radix-16 passes would leave threads idle)
 template <int DIR, bool BFAST, int PADA, int PADB, typename C>
 __device__ int pp_fft_p2(C *A, int abs_, int aes, C *B, int bbs, int bes, int n, int nbatch, const C *T, int tid,
-                         int nthr, int maxlr = 4) {
+                         int nthr, int maxlr = 4, const uint4 *tc = nullptr) {
     const int logn = ilog2(n), lognbatch = ilog2(nbatch);
     int logNs = 0, rem = logn, where = 0;
     const C *Tp = T;
     while (rem > 0) {
         const int lr = rem >= maxlr ? maxlr : rem;   // largest radix first, the rest last
-        if (where == 0) {
+        // (the first pass always runs A -> B)
+        const bool done = logNs == 0 && tc_first_pass<DIR, BFAST, false, PADA, PADB>(
+                                            lr, logNs, A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, tc, tid, nthr);
+        if (done) {
+        } else if (where == 0) {
             if (lr == 4) pp_pass_p2<16, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
             else if (lr == 3) pp_pass_p2<8, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
             else if (lr == 2) pp_pass_p2<4, DIR, BFAST, PADA, PADB>(A, abs_, aes, B, bbs, bes, logn, nbatch, lognbatch, logNs, Tp, tid, nthr);
@@ -427,7 +577,9 @@ __device__ __forceinline__ void pp_pass_p2_adj(const C *src, int sbs, int ses, C
 template <bool BFAST, int PADS, int PADD, typename C>
 __device__ __forceinline__ void pp_pass_p2_adj_r(int lr, const C *src, int sbs, int ses, C *dst, int dbs, int des,
                                                  int logn, int nbatch, int lognbatch, int logNs, const C *T, int tid,
-                                                 int nthr) {
+                                                 int nthr, const uint4 *tc = nullptr) {
+    if (tc_first_pass<+1, BFAST, true, PADS, PADD>(lr, logNs, src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch,
+                                                    tc, tid, nthr)) return;
     if (lr == 4) pp_pass_p2_adj<16, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
     else if (lr == 3) pp_pass_p2_adj<8, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
     else if (lr == 2) pp_pass_p2_adj<4, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
@@ -437,7 +589,9 @@ __device__ __forceinline__ void pp_pass_p2_adj_r(int lr, const C *src, int sbs, 
 template <bool BFAST, int PADS, int PADD, typename C>
 __device__ __forceinline__ void pp_pass_p2_fwd_r(int lr, const C *src, int sbs, int ses, C *dst, int dbs, int des,
                                                  int logn, int nbatch, int lognbatch, int logNs, const C *T, int tid,
-                                                 int nthr) {
+                                                 int nthr, const uint4 *tc = nullptr) {
+    if (tc_first_pass<-1, BFAST, false, PADS, PADD>(lr, logNs, src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch,
+                                                     tc, tid, nthr)) return;
     if (lr == 4) pp_pass_p2<16, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
     else if (lr == 3) pp_pass_p2<8, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
     else if (lr == 2) pp_pass_p2<4, -1, BFAST, PADS, PADD>(src, sbs, ses, dst, dbs, des, logn, nbatch, lognbatch, logNs, T, tid, nthr);
@@ -511,13 +665,13 @@ struct GroupSync {
 // nthr participating threads (sync); callers synchronise before.
 template <bool BFAST, typename C, typename Mult>
 __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *T, const Mult &mult, int tid,
-                          int nthr, const GroupSync &sync) {
+                          int nthr, const GroupSync &sync, const uint4 *tc = nullptr) {
     const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
     int where = 0, lr, lns, toff;
     for (int p = 0; p < L - 1; ++p) {   // forward passes 1 .. L-1
         p2_schedule(logn, p, &lr, &lns, &toff);
-        if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
-        else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
+        else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
         sync();
         where ^= 1;
     }
@@ -535,8 +689,8 @@ __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C
     sync();
     for (int p = L - 2; p >= 0; --p) {   // adjoint passes L-1 .. 1
         p2_schedule(logn, p, &lr, &lns, &toff);
-        if (where == 0) pp_pass_p2_adj_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
-        else pp_pass_p2_adj_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        if (where == 0) pp_pass_p2_adj_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
+        else pp_pass_p2_adj_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
         sync();
         where ^= 1;
     }
@@ -552,13 +706,13 @@ __device__ int pp_conv_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C
 
 template <bool BFAST, typename C>
 __device__ int pp_fwd_head_p2(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *T, int tid, int nthr,
-                              const GroupSync &sync) {
+                              const GroupSync &sync, const uint4 *tc = nullptr) {
     const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
     int where = 0, lr, lns, toff;
     for (int p = 0; p < L - 1; ++p) {
         p2_schedule(logn, p, &lr, &lns, &toff);
-        if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
-        else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        if (where == 0) pp_pass_p2_fwd_r<BFAST, 0, 1>(lr, A, la.bs, la.es, B, lb.bs, lb.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
+        else pp_pass_p2_fwd_r<BFAST, 1, 0>(lr, B, lb.bs, lb.es, A, la.bs, la.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
         sync();
         where ^= 1;
     }
@@ -647,14 +801,14 @@ __device__ void pp_out_fused_p2(const C *X0, const C *X1, Lay lx, bool two, C *Q
 // the result is in Q0, 1 if in Q1
 template <bool BFAST, typename C>
 __device__ int pp_adj_tail_p2(C *Q0, C *Q1, Lay lq, int n, int nbatch, const C *T, int tid, int nthr,
-                              const GroupSync &sync) {
+                              const GroupSync &sync, const uint4 *tc = nullptr) {
     const int logn = ilog2(n), lognbatch = ilog2(nbatch), L = p2_npasses(logn);
     int where = 0, lr, lns, toff;
     for (int p = L - 2; p >= 0; --p) {
         p2_schedule(logn, p, &lr, &lns, &toff);
         C *src = where ? Q1 : Q0, *dst = where ? Q0 : Q1;
-        if (lq.pad) pp_pass_p2_adj_r<BFAST, 1, 1>(lr, src, lq.bs, lq.es, dst, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
-        else pp_pass_p2_adj_r<BFAST, 0, 0>(lr, src, lq.bs, lq.es, dst, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr);
+        if (lq.pad) pp_pass_p2_adj_r<BFAST, 1, 1>(lr, src, lq.bs, lq.es, dst, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
+        else pp_pass_p2_adj_r<BFAST, 0, 0>(lr, src, lq.bs, lq.es, dst, lq.bs, lq.es, logn, nbatch, lognbatch, lns, T + toff, tid, nthr, tc);
         sync();
         where ^= 1;
     }
@@ -668,9 +822,9 @@ __device__ int pp_adj_tail_p2(C *Q0, C *Q1, Lay lq, int n, int nbatch, const C *
 // the shift-based ones, used when n is a power of two)
 template <int DIR, bool BFAST, int PADA, int PADB, typename C>
 __device__ __forceinline__ int pp_fft_any(C *A, Lay la, C *B, Lay lb, int n, int nbatch, const C *W, const C *T,
-                                          int tid, int nthr, int maxlr = 4) {
+                                          int tid, int nthr, int maxlr = 4, const uint4 *tc = nullptr) {
     if (is_pow2(n) && (!BFAST || is_pow2(nbatch)))
-        return pp_fft_p2<DIR, BFAST, PADA, PADB>(A, la.bs, la.es, B, lb.bs, lb.es, n, nbatch, T, tid, nthr, maxlr);
+        return pp_fft_p2<DIR, BFAST, PADA, PADB>(A, la.bs, la.es, B, lb.bs, lb.es, n, nbatch, T, tid, nthr, maxlr, tc);
     return pp_fft<DIR, BFAST>(A, la, B, lb, n, nbatch, W, tid, nthr);
 }
 

@@ -106,11 +106,11 @@ __device__ __forceinline__ real real_at(const typename cplx_of<real>::type *buf,
 // padded rows, a chunk at a time; results always end in A.
 template <int DIR, typename C>
 __device__ void rows_fft_to_A(C *A, Lay la, C *wk, Lay lb, int n, int nrows, int wrows, const C *W, const C *T,
-                              int nthr, int maxlr) {
+                              int nthr, int maxlr, const uint4 *tc) {
     for (int r0 = 0; r0 < nrows; r0 += wrows) {
         const int nb = min(wrows, nrows - r0);
         C *a = A + (size_t)r0 * la.bs;
-        const int w = pp_fft_any<DIR, false, 0, 1>(a, la, wk, lb, n, nb, W, T, (int)threadIdx.x, nthr, maxlr);
+        const int w = pp_fft_any<DIR, false, 0, 1>(a, la, wk, lb, n, nb, W, T, (int)threadIdx.x, nthr, maxlr, tc);
         if (w) {
             for (int i = threadIdx.x; i < nb * n; i += nthr) {
                 const int r = i / n, e = i - r * n;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void k1_issue(const real *f, real *dst, uint64_t *bar
         bulk_g2s(dst + (size_t)r * nx, fr + (size_t)(i0 + r) * N + (size_t)y * nx, rowbytes, bar);
 }
 
-template <typename real, int SMAX>
+template <typename real, int SMAX, bool TC = false>
 __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB) k1_pipe(const real *__restrict__ f,
                                                              typename cplx_of<real>::type *spec,
                                                              real *__restrict__ fields,
@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
                                                              const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
                                                              int ntr, KP<real> P, int CH, int *err) {
+    const uint4 *tc = TC ? P.tc16 : nullptr;   // split-BF16 tensor-core first passes
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_K1>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
         __syncthreads();
         const int r0 = (i0 == 0) ? 1 : 0;   // the rest velocity is not transformed
         if (nf > r0) {
-            const int w = pp_fft_any<-1, false, 0, 1>(Bc + (size_t)r0 * h, la, wk, lb, h, nf - r0, Wr, Tr, tid, NT);
+            const int w = pp_fft_any<-1, false, 0, 1>(Bc + (size_t)r0 * h, la, wk, lb, h, nf - r0, Wr, Tr, tid, NT, 4, tc);
             C *res = w ? wk : Bc + (size_t)r0 * h;
             const Lay lr = w ? lb : la;
             r2c_post_l(res, lr, h, nf - r0, Wp, tid, NT);
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
                 a0[s] = a1[s] = a2[s] = a3[s] = real(0);
             }
             __syncthreads();
-            const int w = pp_fft_any<-1, false, 0, 1>(Bc, la, wk, lb, h, 6, Wr, Tr, tid, NT);
+            const int w = pp_fft_any<-1, false, 0, 1>(Bc, la, wk, lb, h, 6, Wr, Tr, tid, NT, 4, tc);
             C *res = w ? wk : Bc;
             const Lay lr = w ? lb : la;
             r2c_post_l(res, lr, h, 6, Wp, tid, NT);
@@ -405,7 +406,7 @@ __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDes
 
 // MULTI = false: every group has one input and one output in place
 // (convection); MULTI = true: up to 2 inputs and several outputs.
-template <typename real, bool MULTI>
+template <typename real, bool MULTI, bool TC = false>
 __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MINB) kcol_pipe(typename cplx_of<real>::type *spec,
                                                                const GroupDesc *__restrict__ groups, int ngroups,
                                                                const real *__restrict__ kxt,
@@ -414,6 +415,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                                                                const typename cplx_of<real>::type *__restrict__ Tc_g,
                                                                int ntc, KP<real> P, int TW, int BOXR, int nbuf,
                                                                const __grid_constant__ CUtensorMap tmap, int *err) {
+    const uint4 *tc = TC ? P.tc16 : nullptr;   // split-BF16 tensor-core first passes
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_COL>::NT;
     constexpr int NIN = MULTI ? 2 : 1;
@@ -492,21 +494,21 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 // bank conflicts of half-width tiles)
                 const ColMult<real> m{(real)gd.c[0][0][0], (real)gd.c[0][0][1], (real)gd.c[0][0][2],
                                       (real)gd.c[0][0][3], (real)gd.c[0][0][4], scale, kxs, kys, kx0};
-                const int w = pp_conv_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, m, tid, NT, GroupSync{0, NT});
+                const int w = pp_conv_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, m, tid, NT, GroupSync{0, NT}, tc);
                 R = w ? wk0 : in0;
                 lr = w ? lw : lt;
             } else {
                 // convection (the tile holding k_x = 0 pairs (k_y, -k_y) of the
                 // packed DC / row-Nyquist column; other lengths): forward,
                 // multiply in place, inverse
-                const int w1 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
+                const int w1 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT, 4, tc);
                 C *X = w1 ? wk0 : in0;
                 C *Y = w1 ? in0 : wk0;
                 const Lay lx = w1 ? lw : lt, ly = w1 ? lt : lw;
                 col_multiply<real>(X, lx, X, lx, X, lx, gd, 0, kxs, kys, kx0, TW, lgTW, ny, h, scale, NT);
                 __syncthreads();
-                const int w2 = w1 ? pp_fft_any<+1, true, 1, 0>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT)
-                                  : pp_fft_any<+1, true, 0, 1>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT);
+                const int w2 = w1 ? pp_fft_any<+1, true, 1, 0>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT, 4, tc)
+                                  : pp_fft_any<+1, true, 0, 1>(X, lx, Y, ly, ny, TW, Wc, Tc, tid, NT, 4, tc);
                 R = w2 ? Y : X;
                 lr = w2 ? ly : lx;
             }
@@ -522,8 +524,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 // {in1, wk1}); each output: one fused pass into the free pair
                 // of buffers, then the adjoint passes L-1 .. 1
                 const GroupSync bs{0, NT};
-                const int wx = pp_fwd_head_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, tid, NT, bs);
-                if (gd.nin > 1) pp_fwd_head_p2<true>(in1, lt, wk1, lw, ny, TW, Tc, tid, NT, bs);
+                const int wx = pp_fwd_head_p2<true>(in0, lt, wk0, lw, ny, TW, Tc, tid, NT, bs, tc);
+                if (gd.nin > 1) pp_fwd_head_p2<true>(in1, lt, wk1, lw, ny, TW, Tc, tid, NT, bs, tc);
                 const C *X0 = wx ? wk0 : in0, *X1 = wx ? wk1 : in1;
                 const Lay lx = wx ? lw : lt;
                 C *Q0 = wx ? in0 : wk0, *Q1 = wx ? in1 : wk1;
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                     m.kys = kys;
                     m.kx0 = kx0;
                     pp_out_fused_p2<true>(X0, X1, lx, gd.nin > 1, Q0, lq, ny, TW, Tc, m, tid, NT, bs);
-                    const int wq = pp_adj_tail_p2<true>(Q0, Q1, lq, ny, TW, Tc, tid, NT, bs);
+                    const int wq = pp_adj_tail_p2<true>(Q0, Q1, lq, ny, TW, Tc, tid, NT, bs, tc);
                     const C *R = wq ? Q1 : Q0;
                     gout = spec_r + (size_t)gd.out_slot[o] * slot + kx0;
                     for (int idx = tid; idx < tile; idx += NT) {
@@ -554,14 +556,14 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
             } else {
             // X0 in {in0, wk0}, X1 in {in1, wk1}; outputs ping-pong between
             // the two buffers left free
-            const int w0 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT);
+            const int w0 = pp_fft_any<-1, true, 0, 1>(in0, lt, wk0, lw, ny, TW, Wc, Tc, tid, NT, 4, tc);
             C *X0 = w0 ? wk0 : in0;
             C *F0 = w0 ? in0 : wk0;
             const Lay lx0 = w0 ? lw : lt, lf0 = w0 ? lt : lw;
             C *X1 = in1, *F1 = wk1;
             Lay lx1 = lt, lf1 = lw;
             if (gd.nin > 1) {
-                const int w1 = pp_fft_any<-1, true, 0, 1>(in1, lt, wk1, lw, ny, TW, Wc, Tc, tid, NT);
+                const int w1 = pp_fft_any<-1, true, 0, 1>(in1, lt, wk1, lw, ny, TW, Wc, Tc, tid, NT, 4, tc);
                 X1 = w1 ? wk1 : in1;
                 F1 = w1 ? in1 : wk1;
                 lx1 = w1 ? lw : lt;
@@ -571,10 +573,10 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 col_multiply<real>(F0, lf0, X0, lx0, X1, lx1, gd, o, kxs, kys, kx0, TW, lgTW, ny, h, scale, NT);
                 __syncthreads();
                 int w2;
-                if (lf0.pad) w2 = lf1.pad ? pp_fft_any<+1, true, 1, 1>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT)
-                                          : pp_fft_any<+1, true, 1, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT);
-                else w2 = lf1.pad ? pp_fft_any<+1, true, 0, 1>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT)
-                                  : pp_fft_any<+1, true, 0, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT);
+                if (lf0.pad) w2 = lf1.pad ? pp_fft_any<+1, true, 1, 1>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT, 4, tc)
+                                          : pp_fft_any<+1, true, 1, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT, 4, tc);
+                else w2 = lf1.pad ? pp_fft_any<+1, true, 0, 1>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT, 4, tc)
+                                  : pp_fft_any<+1, true, 0, 0>(F0, lf0, F1, lf1, ny, TW, Wc, Tc, tid, NT, 4, tc);
                 const C *R = w2 ? F1 : F0;
                 const Lay lr = w2 ? lf1 : lf0;
                 gout = spec_r + (size_t)gd.out_slot[o] * slot + kx0;
@@ -603,13 +605,14 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
 
 constexpr int NT3 = 256;
 
-template <typename real>
+template <typename real, bool TC = false>
 __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spec, const real *__restrict__ fields,
                                                real *__restrict__ aux,
                                                const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                const typename cplx_of<real>::type *__restrict__ Tr_g, int ntr,
                                                KP<real> P, int WR, int maxlr, int *err) {
+    const uint4 *tc = TC ? P.tc16 : nullptr;   // split-BF16 tensor-core first passes
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -650,7 +653,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     }
     c2r_pre_l(d, la, h, ND1, Wp, tid, NT3);
     __syncthreads();
-    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, Tr, NT3, maxlr);
+    rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, Tr, NT3, maxlr, tc);
     const C *res = d;
     const Lay lr = la;
     real *dw = reinterpret_cast<real *>(d);
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
         dw[4 * nx + x] = q2 * Ty;
     }
     __syncthreads();
-    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, Tr, NT3, maxlr);
+    rows_fft_to_A<-1>(d, la, wk, lb, h, 5, WR, Wr, Tr, NT3, maxlr, tc);
     C *res2 = d;
     const Lay lr2 = la;
     r2c_post_l(res2, lr2, h, 5, Wp, tid, NT3);
@@ -741,7 +744,7 @@ __device__ __forceinline__ void k5_issue_head(const typename cplx_of<real>::type
 
 // NHB head buffers (1 or 2): the head of row ri lives in buffer ri % NHB and
 // is prefetched NHB rows ahead.
-template <typename real, int SMAX>
+template <typename real, int SMAX, bool TC = false>
 __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB) k5_pipe(const typename cplx_of<real>::type *spec,
                                                              const real *__restrict__ fields,
                                                              const real *__restrict__ aux, const real *fcur,
@@ -751,6 +754,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
                                                              int ntr, KP<real> P, int CH, int NHB, int nbuf, int maxlr,
                                                              int *err) {
+    const uint4 *tc = TC ? P.tc16 : nullptr;   // split-BF16 tensor-core first passes
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_K5>::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -822,7 +826,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
             C *l2 = reinterpret_cast<C *>(H);
             c2r_pre_l(l2, la, h, 3, Wp, tid, NT);
             __syncthreads();
-            const int w = pp_fft_any<+1, false, 0, 1>(l2, la, wk, lb, h, 3, Wr, Tr, tid, NT, maxlr);
+            const int w = pp_fft_any<+1, false, 0, 1>(l2, la, wk, lb, h, 3, Wr, Tr, tid, NT, maxlr, tc);
             const C *lres = w ? wk : l2;
             const Lay llr = w ? lb : la;
             // per-site coefficients, written over the head rows (same site,
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         C *Bc = reinterpret_cast<C *>(B);
         c2r_pre_l(Bc, la, h, nv, Wp, tid, NT);
         __syncthreads();
-        const int w = pp_fft_any<+1, false, 0, 1>(Bc, la, wk, lb, h, nv, Wr, Tr, tid, NT, maxlr);
+        const int w = pp_fft_any<+1, false, 0, 1>(Bc, la, wk, lb, h, nv, Wr, Tr, tid, NT, maxlr, tc);
         const C *cres = w ? wk : Bc;
         const Lay lcr = w ? lb : la;
 #pragma unroll 1

@@ -128,6 +128,10 @@ def torch_float64():
     return torch.float64
 
 
+# precision flag: fp32 with split-BF16 tensor-core first radix-16 passes
+BF16SPLIT = 256
+
+
 def params(nx, ny, dx=1.0 / 256, dt=1e-5, tau=1e-2, a=9.0 / 8.0, b=1.0 / 3.0, K=1e-5, H=0.0,
            q=-0.004, zeta=0.0, window=4, integrator=3, precision=64, check_every=0):
     """fftlb_params with the paper's defaults (Sec. 3)."""

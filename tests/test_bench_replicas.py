@@ -67,8 +67,9 @@ def test_ncu_traffic_summary_from_a_launch_csv(tmp_path):
     import bench
     hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
           '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
-    names = ["void k1_pipe<float, 4>(x)", "void kcol_pipe<float, 0>(x)", "void kcol_pipe<float, 1>(x)",
-             "void k3_pipe<float>(x)", "void kcol_pipe<float, 1>(x)", "void k5_pipe<float, 2>(x)"]
+    names = ["void k1_pipe<float, 4, false>(x)", "void kcol_pipe<float, false, false>(x)",
+             "void kcol_pipe<float, true, false>(x)", "void k3_pipe<float, false>(x)",
+             "void kcol_pipe<float, true, false>(x)", "void k5_pipe<float, 2, false>(x)"]
     lines = ["==PROF== noise\n", hdr]
     for stage in range(2):
         for j, nm in enumerate(names):

@@ -31,7 +31,8 @@ def spinodal_case(n, Tr, precision, seed):
 def test_batch_matches_single_handles(fl):
     cases = [slab_case(64, 0.9, 64, 1), slab_case(48, 0.8, 64, 2), slab_case(128, 0.95, 32, 3),
              slab_case(96, 0.75, 32, 4), spinodal_case(256, 0.8, 32, 5), spinodal_case(384, 0.9, 32, 6),
-             slab_case(128, 0.85, 32, 7)]
+             slab_case(128, 0.85, 32, 7), spinodal_case(256, 0.8, 32 | fl.BF16SPLIT, 8),
+             slab_case(128, 0.85, 32 | fl.BF16SPLIT, 9)]
     with fl.Batch([fl.params(**kw) for _, kw in cases], autotune=True) as b:
         for r, (fields, _) in enumerate(cases):
             b.set_fields(r, *fields)

@@ -150,7 +150,7 @@ def _spinodal_oracle(n, nsteps):
     return fields, kw, f
 
 
-def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3):
+def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u_split=0.0):
     """Elementwise bound on |df_i| / f_i of the FP32 path after nsteps RK3
     steps.  Two sources: (1) each stage update rounds f_i at most twice, and
     the initial f^eq once: 4 (S + 1) u with a factor 2 of margin; (2) the
@@ -162,10 +162,12 @@ def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3):
     spectrum of the window-4 symbol (max k_max = (2/dx)(1 + 1/6 + 3/40 +
     5/112)) the rms of |k|^3 is 0.83 k_max^3.  |v - u| |dB| dt per stage,
     over S = 3 nsteps stages, times sqrt(2 ln M) for the maximum over the M
-    values of f, times 2 of margin."""
+    values of f, times 2 of margin.  u_split: the relative error of one
+    split-BF16 first pass (the row and the column first passes of a 2-D
+    transform add 2 u_split to its u sqrt(log2 N))."""
     u, N, S = 2.0 ** -24, n * n, 3 * nsteps
     kmax = (2 / dx) * (1 + 1 / 6 + 3 / 40 + 5 / 112)
-    eps = u * np.sqrt(np.log2(N)) * np.sqrt(np.mean(rho ** 2))
+    eps = (u * np.sqrt(np.log2(N)) + 2 * u_split) * np.sqrt(np.mean(rho ** 2))
     d3 = 2 * eps * 0.83 * kmax ** 3
     dB = vmax * K * d3 / T.min()
     tail = np.sqrt(2 * np.log(33 * N))
@@ -191,6 +193,47 @@ def test_spinodal_sweep_grids(fl, n, nsteps, precision):
         err = (np.abs(f_g - f_o) / np.abs(f_o)).max()
         print(f"fp32 {n}^2 after {nsteps} RK3 steps: max |df|/f = {err:.3e} (bound {bound:.3e})")
         assert err < bound
+
+
+# one split-BF16 first pass: |x - x_hi - x_lo| <= 2^-16 |x| for each operand
+# (x_hi = bf16(x), x_lo = bf16(x - x_hi), nearest even) and the dropped
+# W_lo x_lo <= 2^-16 |W| |x|
+U_SPLIT = 3 * 2.0 ** -16
+
+
+@pytest.mark.parametrize("n,nsteps", [(256, 3), (512, 1)])
+def test_bf16split_spinodal(fl, n, nsteps):
+    """precision 32 | BF16SPLIT: the first radix-16 pass of every power-of-two
+    row and column transform is the split-BF16 DFT product on the tensor
+    cores.  Element by element against the oracle within fp32_force_bound
+    with that pass's rounding, and visibly apart from the plain fp32 path
+    (the tensor-core pass ran: its 2^-16 rounding shows in f)."""
+    fields, kw, f_o = _spinodal_oracle(n, nsteps)
+    out = {}
+    for prec in (32, 32 | fl.BF16SPLIT):
+        with fl.Handle(fl.params(integrator=3, precision=prec, **kw)) as h:
+            h.set_fields(*fields)
+            h.step(nsteps)
+            out[prec] = h.get_f()
+    e32 = (np.abs(out[32] - f_o) / np.abs(f_o)).max()
+    es = (np.abs(out[32 | fl.BF16SPLIT] - f_o) / np.abs(f_o)).max()
+    bound = fp32_force_bound(n, nsteps, fields[0], fields[3], u_split=U_SPLIT)
+    print(f"{n}^2, {nsteps} RK3 steps: max |df|/f fp32 {e32:.3e}, split-BF16 {es:.3e} (bound {bound:.3e})")
+    assert es < bound
+    assert es > e32
+
+
+def test_bf16split_leaves_other_lengths_unchanged(fl):
+    """384 = 3 * 2^7 takes the mixed-radix passes in rows and columns, where
+    the split mode changes nothing: identical to the fp32 path bit for bit."""
+    fields, kw, _ = _spinodal_oracle(384, 3)
+    out = []
+    for prec in (32, 32 | fl.BF16SPLIT):
+        with fl.Handle(fl.params(integrator=3, precision=prec, **kw)) as h:
+            h.set_fields(*fields)
+            h.step(1)
+            out.append(h.get_f())
+    assert np.array_equal(out[0], out[1])
 
 
 def test_torch_cufft_reference_matches_oracle():

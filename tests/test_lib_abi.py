@@ -43,7 +43,8 @@ def test_params_struct_layout_matches_header(fl):
 
 
 @pytest.mark.parametrize("kw", [dict(nx=10), dict(ny=6 * 5), dict(nx=2), dict(tau=0.0), dict(window=5),
-                                dict(integrator=2), dict(precision=16)])
+                                dict(integrator=2), dict(precision=16), dict(precision=256),
+                                dict(precision=64 | 256)])
 def test_create_rejects_bad_arguments_without_device_work(fl, kw):
     base = dict(nx=16, ny=16)
     base.update(kw)
@@ -52,6 +53,11 @@ def test_create_rejects_bad_arguments_without_device_work(fl, kw):
         fl.Handle(p)
     assert ei.value.status == fl.ERR_ARG
     assert len(str(ei.value)) > 10
+
+
+def test_bf16split_flag_matches_header(fl):
+    src = open(os.path.join(ROOT, "include", "fftlb.h")).read()
+    assert int(re.search(r"#define FFTLB_BF16SPLIT (\d+)", src).group(1)) == fl.BF16SPLIT
 
 
 def test_null_handle_calls_return_arg_error(fl):
