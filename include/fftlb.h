@@ -80,7 +80,9 @@ typedef struct {
 
 /* Velocity set of Eq. 1: nspeeds rings of ndirs directions.  Only
  * nspeeds = 4, ndirs = 8 is supported; speeds = NULL selects the paper's
- * (1.0, 1.9, 2.9, 4.3). */
+ * (1.0, 1.9, 2.9, 4.3).  The set lives in device constant memory shared by
+ * all handles (and batches) of one precision in the process: while any of
+ * them is alive, a create with other speeds fails with FFTLB_ERR_ARG. */
 typedef struct {
     int nspeeds;
     const double *speeds;
@@ -90,7 +92,8 @@ typedef struct {
 /* Create a handle for problem *p on the current CUDA device.  velset may be
  * NULL (paper's set).  cuda_stream is a cudaStream_t (may be NULL).
  * Allocates ~ (2*33 + 38 + 15 + 5 + 7) nx ny values of the chosen precision.
- * Errors: FFTLB_ERR_ARG (sizes, tau <= 0, window, integrator, precision),
+ * Errors: FFTLB_ERR_ARG (sizes, tau <= 0, window, integrator, precision,
+ * a velocity set other than that of live handles of the same precision),
  * FFTLB_ERR_OOM, FFTLB_ERR_CUDA.  On error *h is set to NULL. */
 fftlb_status fftlb_create(fftlb_t *h, const fftlb_params *p,
                           const fftlb_velset *velset, void *cuda_stream);

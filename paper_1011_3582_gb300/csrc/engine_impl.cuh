@@ -37,6 +37,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -58,12 +59,21 @@ constexpr int NSLOT = 58;
 enum { D_RX, D_RY, D_LAP, D_UXX, D_UXY, D_UYX, D_UYY, D_DIVX, D_DIVY, D_TX, D_TY, D_PIX, D_PIY, D_GX, D_GY };
 
 // velocity set (Eq. 1) and weight-polynomial coefficients (Eq. 4); each
-// translation unit holds its own copy
+// translation unit holds its own copy, shared by all live engines of that
+// unit, which must therefore use one velocity set (vs_owner below)
 static __constant__ double c_vx[Q], c_vy[Q], c_v2[Q];
 static __constant__ float c_vxf[Q], c_vyf[Q], c_v2f[Q];
 static __constant__ int c_ring[Q];
 static __constant__ double c_Fk[4][4];    // F_k = T (c3 + T (c2 + T (c1 + T c0)))
 static __constant__ float c_Fkf[4][4];
+
+// the live engines of this translation unit and their velocity set
+struct VelocitySetOwner {
+    std::mutex mu;
+    int live = 0;
+    double speeds[4] = {0, 0, 0, 0};
+};
+static VelocitySetOwner vs_owner;
 
 template <typename real> __device__ __forceinline__ real VX(int i);
 template <> __device__ __forceinline__ double VX<double>(int i) { return c_vx[i]; }
@@ -470,6 +480,10 @@ class EngineT : public Engine {
             cudaEventDestroy(e.b);
         }
         release();
+        if (vs_counted_) {
+            std::lock_guard<std::mutex> g(vs_owner.mu);
+            --vs_owner.live;
+        }
     }
 
     Status init(const fftlb_params &p, const double speeds[4], cudaStream_t s, int nrun) override {
@@ -488,9 +502,20 @@ class EngineT : public Engine {
         ny_ = p.ny;
         h_ = nx_ / 2;
         N_ = (size_t)nx_ * ny_;
-        Status st = upload_constants(speeds);
-        if (!st.good()) return st;
-        st = alloc();
+        {
+            // the velocity constants are per translation unit: a second set
+            // would overwrite the one live engines compute with
+            std::lock_guard<std::mutex> g(vs_owner.mu);
+            if (vs_owner.live > 0 && memcmp(vs_owner.speeds, speeds, sizeof vs_owner.speeds) != 0)
+                return Status::err(FFTLB_ERR_ARG, "velocity set: live handles of this precision use another set of "
+                                                  "speeds (one velocity set per precision at a time)");
+            Status su = upload_constants(speeds);
+            if (!su.good()) return su;
+            memcpy(vs_owner.speeds, speeds, sizeof vs_owner.speeds);
+            ++vs_owner.live;
+            vs_counted_ = true;
+        }
+        Status st = alloc();
         if (!st.good()) return st;
         st = build_tables();
         if (!st.good()) return st;
@@ -643,6 +668,7 @@ class EngineT : public Engine {
     C *Wr_ = nullptr, *Wp_ = nullptr, *Wc_ = nullptr;
     C *Tr_ = nullptr, *Tc_ = nullptr;   // pass twiddle tables (power-of-two lengths), radix 16 first
     C *Tr8_ = nullptr;                  // rows, radix 8 first
+    bool vs_counted_ = false;           // counted in vs_owner.live
     static constexpr bool split_ = SPLIT && sizeof(real) == 4;   // split-BF16 tensor-core first passes
     uint4 *tc16_ = nullptr;             // their A fragments (dft16_fragments)
     int ntr_ = 0, ntc_ = 0, ntr8_ = 0;

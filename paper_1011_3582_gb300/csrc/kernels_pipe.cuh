@@ -742,6 +742,23 @@ __device__ __forceinline__ void k5_issue_head(const typename cplx_of<real>::type
         bulk_g2s(dst + (size_t)(7 + r) * nx, aux + (size_t)r * N + (size_t)y * nx, rowbytes, bar);
 }
 
+// cos(r pi / 4) a + sin(r pi / 4) b for direction r of a ring of Eq. 1 (r a
+// compile-time constant after unrolling)
+template <typename real>
+__device__ __forceinline__ real dir_dot(int r, real a, real b) {
+    const real h = real(0.70710678118654752440);
+    switch (r & 7) {
+        case 0: return a;
+        case 1: return h * (a + b);
+        case 2: return b;
+        case 3: return h * (b - a);
+        case 4: return -a;
+        case 5: return -h * (a + b);
+        case 6: return -b;
+        default: return h * (a - b);
+    }
+}
+
 // NHB head buffers (1 or 2): the head of row ri lives in buffer ri % NHB and
 // is prefetched NHB rows ahead.
 template <typename real, int SMAX, bool TC = false>
@@ -830,7 +847,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
             const C *lres = w ? wk : l2;
             const Lay llr = w ? lb : la;
             // per-site coefficients, written over the head rows (same site,
-            // same thread): row 0 <- e0, 1 <- e1x, 2 <- e1y, 7 <- C + C_q
+            // same thread): row 0 <- e0, 1 <- e1x, 2 <- e1y, 7 <- C + C_q,
+            // 8 <- 1 / T
 #pragma unroll 1
             for (int s = 0; s < SMAX; ++s) {
                 const int x = tid + s * NT;
@@ -851,6 +869,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
                     H[nx + x] = Bx - real(2) * CC * ux;
                     H[2 * nx + x] = By - real(2) * CC * uy;
                     H[7 * nx + x] = CC;
+                    H[8 * nx + x] = real(1) / T;
                     // rest velocity (no convection)
                     real F[5];
                     weights_Fk<real>(T, F);
@@ -886,48 +905,92 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
         const int w = pp_fft_any<+1, false, 0, 1>(Bc, la, wk, lb, h, nv, Wr, Tr, tid, NT, maxlr, tc);
         const C *cres = w ? wk : Bc;
         const Lay lcr = w ? lb : la;
+        if (CH == 8) {
+            // the chunk is ring c + 1 (velocities 1 + 8c .. 8 + 8c, Eq. 1):
+            // one speed, one weight F_k, and directions known at compile time
+            const int k = c;
+            const real sk = VX<real>(1 + v0), sk2 = V2<real>(1 + v0);   // direction 0: v = (s_k, 0)
 #pragma unroll 1
-        for (int s = 0; s < SMAX; ++s) {
-            const int x = tid + s * NT;
-            if (x >= nx) continue;
-            real fc[CHMAX5], fb[CHMAX5];
-            const size_t o0 = fo + (size_t)(1 + v0) * N + (size_t)y * nx + x;
-            const real *pc = fcur + o0;
-            const real *pb = fbase + o0;
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x >= nx) continue;
+                real fc[8], fb[8];
+                const size_t o0 = fo + (size_t)(1 + v0) * N + (size_t)y * nx + x;
+                const real *pc = fcur + o0;
+                const real *pb = fbase + o0;
 #pragma unroll
-            for (int r = 0; r < CHMAX5; ++r) {
-                if (r < nv) {
+                for (int r = 0; r < 8; ++r) {
                     fc[r] = pc[r * N];
                     fb[r] = with_base ? pb[r * N] : real(0);
                 }
-            }
-            real *po = fout + o0;
-            const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
-            const real e0 = H[x], e1x = H[nx + x], e1y = H[2 * nx + x], CC = H[7 * nx + x];
-            real F[5];
-            weights_Fk<real>(T, F);                                  // Eqs. 4-6
-            const real iT = real(1) / T, qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
-            const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
-            const real p3 = iT * iT * iT / real(6), p4 = iT * iT * iT * iT / real(24);
+                real *po = fout + o0;
+                const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
+                const real iT = H[8 * nx + x];
+                const real e0 = H[x], e1x = H[nx + x], e1y = H[2 * nx + x], CC = H[7 * nx + x];
+                const real Fk = T * (FKC<real>(k, 3) + T * (FKC<real>(k, 2) + T * (FKC<real>(k, 1) + T * FKC<real>(k, 0))));   // Eq. 4
+                const real qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
+                const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
+                const real p3 = iT * iT * iT * (real(1) / real(6)), p4 = iT * iT * iT * iT * (real(1) / real(24));
+                const real rF = rho * Fk;
+                const real g0 = e0 + CC * sk2;   // e0 + CC |v|^2 on the ring
+                const real uxk = sk * ux, uyk = sk * uy, exk = sk * e1x, eyk = sk * e1y;
 #pragma unroll
-            for (int r = 0; r < CHMAX5; ++r) {
-                if (r < nv) {
-                    const int i = 1 + v0 + r;
-                    const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
-                    const int k = c_ring[i];
-                    const real vu = vx * ux + vy * uy;
+                for (int r = 0; r < 8; ++r) {
+                    const real vu = dir_dot<real>(r, uxk, uyk);
                     const real br = p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4)));
-                    real rF = F[1];
-                    rF = (k == 2) ? F[2] : rF;
-                    rF = (k == 3) ? F[3] : rF;
-                    rF = (k == 4) ? F[4] : rF;
-                    const real fe = rho * rF * br;                                          // Eq. 3
-                    const real I = -(e0 + e1x * vx + e1y * vy + CC * v2) * fe;              // Eq. 11
+                    const real fe = rF * br;                                                 // Eq. 3
+                    const real I = -(g0 + dir_dot<real>(r, exk, eyk)) * fe;                   // Eq. 11
                     const real conv = real_at<real>(cres, lcr, r, x);
-                    const real rhs = -conv - (fc[r] - fe) * itau + I;                       // Eq. 10
+                    const real rhs = -conv - (fc[r] - fe) * itau + I;                        // Eq. 10
                     real fn = beta * (fc[r] + dt * rhs);
                     if (with_base) fn += alpha * fb[r];
                     po[r * N] = fn;
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x >= nx) continue;
+                real fc[CHMAX5], fb[CHMAX5];
+                const size_t o0 = fo + (size_t)(1 + v0) * N + (size_t)y * nx + x;
+                const real *pc = fcur + o0;
+                const real *pb = fbase + o0;
+#pragma unroll
+                for (int r = 0; r < CHMAX5; ++r) {
+                    if (r < nv) {
+                        fc[r] = pc[r * N];
+                        fb[r] = with_base ? pb[r * N] : real(0);
+                    }
+                }
+                real *po = fout + o0;
+                const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
+                const real e0 = H[x], e1x = H[nx + x], e1y = H[2 * nx + x], CC = H[7 * nx + x];
+                real F[5];
+                weights_Fk<real>(T, F);                                  // Eqs. 4-6
+                const real iT = H[8 * nx + x], qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
+                const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
+                const real p3 = iT * iT * iT * (real(1) / real(6)), p4 = iT * iT * iT * iT * (real(1) / real(24));
+#pragma unroll
+                for (int r = 0; r < CHMAX5; ++r) {
+                    if (r < nv) {
+                        const int i = 1 + v0 + r;
+                        const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
+                        const int k = c_ring[i];
+                        const real vu = vx * ux + vy * uy;
+                        const real br = p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4)));
+                        real rF = F[1];
+                        rF = (k == 2) ? F[2] : rF;
+                        rF = (k == 3) ? F[3] : rF;
+                        rF = (k == 4) ? F[4] : rF;
+                        const real fe = rho * rF * br;                                          // Eq. 3
+                        const real I = -(e0 + e1x * vx + e1y * vy + CC * v2) * fe;              // Eq. 11
+                        const real conv = real_at<real>(cres, lcr, r, x);
+                        const real rhs = -conv - (fc[r] - fe) * itau + I;                       // Eq. 10
+                        real fn = beta * (fc[r] + dt * rhs);
+                        if (with_base) fn += alpha * fb[r];
+                        po[r * N] = fn;
+                    }
                 }
             }
         }

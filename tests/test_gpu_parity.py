@@ -141,6 +141,43 @@ def test_unstable_state_is_reported_not_trapped(fl):
         assert ei.value.steps_done == 1
 
 
+# a velocity set other than the paper's (1, 1.9, 2.9, 4.3)
+SPEEDS_B = (1.0, 2.0, 3.0, 4.5)
+
+
+def test_custom_velocity_set_fp64(fl):
+    """Speeds 1, 2, 3, 4.5 on the rings of Eq. 1: the weights (Eqs. 4-6), the
+    equilibrium and every velocity-dependent term follow the speeds.  FP64
+    against the oracle run with the same set, 20 RK3 steps, 1e-9."""
+    fields, kw = slab64()
+    p = oracle_params(kw, integrator=3, speeds=SPEEDS_B)
+    f_o = O.run(O.init_equilibrium(*fields, p), p, 20)
+    with fl.Handle(fl.params(precision=64, integrator=3, **kw), speeds=SPEEDS_B) as h:
+        h.set_fields(*fields)
+        h.step(20)
+        f_g = h.get_f()
+    assert rel_err(f_g, f_o) < 1e-9
+
+
+def test_velocity_set_is_one_per_precision(fl):
+    """The velocity set lives in constant memory shared by the handles of one
+    precision: another set is refused while a handle of that precision is
+    alive, accepted for the other precision and after the last one closed."""
+    import gc
+    gc.collect()
+    kw = dict(nx=32, ny=32)
+    with fl.Handle(fl.params(precision=64, **kw)):
+        with pytest.raises(fl.FFTLBError) as ei:
+            fl.Handle(fl.params(precision=64, **kw), speeds=SPEEDS_B)
+        assert ei.value.status == fl.ERR_ARG
+        with fl.Handle(fl.params(precision=32, **kw), speeds=SPEEDS_B):
+            pass
+        with fl.Handle(fl.params(precision=64, **kw)):
+            pass
+    with fl.Handle(fl.params(precision=64, **kw), speeds=SPEEDS_B):
+        pass
+
+
 @functools.lru_cache(maxsize=None)
 def _spinodal_oracle(n, nsteps):
     kw = dict(nx=n, ny=n, a=A49, b=B21)
