@@ -31,9 +31,15 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a
 #ifndef FFTLB_NO_PACKED_F32X2
 // fp32 complex add / subtract as one packed FP32x2 instruction (sm_100+)
 template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+#ifdef FFTLB_CSUB_FFMA2
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);   // a - b, one rounding
+}
+#else
 template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
     return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
+#endif
 #endif
 // i * a and -i * a
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return C{-a.y, a.x}; }
@@ -245,8 +251,12 @@ __host__ __device__ inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) =
 
 // Power-of-two version of pp_pass: n, Ns and (with BFAST) nbatch are powers
 // of two, so the butterfly decomposition uses shifts and masks, and element
-// addresses advance by constant strides (the padded index e + e/16 is
-// linear in t whenever the stride n/R or Ns is a multiple of 16).
+// addresses advance by constant strides.  The padded index p(e) = e + e/16
+// of the R elements s + t S of a butterfly is p(s) + t (S + S/16) when the
+// stride S (n/R or Ns) is a multiple of 16, and p(s) + t S when all R
+// elements lie in one 16-element block (S R <= 16: the block of S R
+// elements starts at a multiple of S R, which divides 16); otherwise each
+// index is padded on its own.
 template <int R, int DIR, bool BFAST, int PADS, int PADD, typename C>
 __device__ __forceinline__ void pp_pass_p2(const C *src, int sbs, int ses, C *dst, int dbs, int des, int logn,
                                            int nbatch, int lognbatch, int logNs, const C *T, int tid, int nthr) {
@@ -255,8 +265,8 @@ __device__ __forceinline__ void pp_pass_p2(const C *src, int sbs, int ses, C *ds
     const int nb = 1 << lognb;
     const int Ns = 1 << logNs;
     const int total = nbatch << lognb;
-    const bool rlin = !PADS || nb >= 16;
-    const bool wlin = !PADD || Ns >= 16;
+    const bool rlin = !PADS || nb >= 16 || (nb << LR) <= 16;
+    const bool wlin = !PADD || Ns >= 16 || (Ns << LR) <= 16;
     const int rstep = (PADS ? nb + (nb >> 4) : nb) * ses;
     const int wstep = (PADD ? Ns + (Ns >> 4) : Ns) * des;
     for (int J = tid; J < total; J += nthr) {
@@ -543,6 +553,11 @@ __device__ __forceinline__ void pp_pass_p2_adj(const C *src, int sbs, int ses, C
     const int nb = 1 << lognb;
     const int Ns = 1 << logNs;
     const int total = nbatch << lognb;
+    // the linear cases of pp_pass_p2, with reads and writes exchanged
+    const bool rlin = !PADS || Ns >= 16 || (Ns << LR) <= 16;
+    const bool wlin = !PADD || nb >= 16 || (nb << LR) <= 16;
+    const int rstep = (PADS ? Ns + (Ns >> 4) : Ns) * ses;
+    const int wstep = (PADD ? nb + (nb >> 4) : nb) * des;
     for (int J = tid; J < total; J += nthr) {
         int b, jj;
         if (BFAST) {
@@ -555,10 +570,16 @@ __device__ __forceinline__ void pp_pass_p2_adj(const C *src, int sbs, int ses, C
         const int k = jj & (Ns - 1);
         const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
         C v[R];
+        if (rlin) {
+            const C *p = src + b * sbs + (PADS ? idxD + (idxD >> 4) : idxD) * ses;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const int e = idxD + t * Ns;
-            v[t] = src[b * sbs + (PADS ? e + (e >> 4) : e) * ses];
+            for (int t = 0; t < R; ++t) v[t] = p[t * rstep];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = idxD + t * Ns;
+                v[t] = src[b * sbs + (e + (e >> 4)) * ses];
+            }
         }
         SmallDFT<R, +1, C>::run(v);
         if (Ns > 1) {
@@ -566,10 +587,16 @@ __device__ __forceinline__ void pp_pass_p2_adj(const C *src, int sbs, int ses, C
 #pragma unroll
             for (int t = 1; t < R; ++t) v[t] = cmul(v[t], cconj(tw[t * Ns]));
         }
+        if (wlin) {
+            C *q = dst + b * dbs + (PADD ? jj + (jj >> 4) : jj) * des;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const int e = jj + t * nb;
-            dst[b * dbs + (PADD ? e + (e >> 4) : e) * des] = v[t];
+            for (int t = 0; t < R; ++t) q[t * wstep] = v[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = jj + t * nb;
+                dst[b * dbs + (e + (e >> 4)) * des] = v[t];
+            }
         }
     }
 }
@@ -610,6 +637,8 @@ __device__ __forceinline__ void pp_pass_p2_fused(C *buf, int bs, int es, int log
     const int nb = 1 << lognb;
     const int Ns = 1 << logNs;
     const int total = nbatch << lognb;
+    const bool lin = !PAD || nb >= 16 || (nb << LR) <= 16;   // as in pp_pass_p2
+    const int step = (PAD ? nb + (nb >> 4) : nb) * es;
     for (int J = tid; J < total; J += nthr) {
         int b, jj;
         if (BFAST) {
@@ -621,11 +650,17 @@ __device__ __forceinline__ void pp_pass_p2_fused(C *buf, int bs, int es, int log
         }
         const int k = jj & (Ns - 1);
         const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
+        C *p = buf + b * bs + (PAD ? jj + (jj >> 4) : jj) * es;
         C v[R];
+        if (lin) {
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const int e = jj + t * nb;
-            v[t] = buf[b * bs + (PAD ? e + (e >> 4) : e) * es];
+            for (int t = 0; t < R; ++t) v[t] = p[t * step];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = jj + t * nb;
+                v[t] = buf[b * bs + (e + (e >> 4)) * es];
+            }
         }
         const C *tw = T + k;
         if (Ns > 1) {
@@ -640,10 +675,15 @@ __device__ __forceinline__ void pp_pass_p2_fused(C *buf, int bs, int es, int log
 #pragma unroll
             for (int t = 1; t < R; ++t) v[t] = cmul(v[t], cconj(tw[t * Ns]));
         }
+        if (lin) {
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const int e = jj + t * nb;
-            buf[b * bs + (PAD ? e + (e >> 4) : e) * es] = v[t];
+            for (int t = 0; t < R; ++t) p[t * step] = v[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = jj + t * nb;
+                buf[b * bs + (e + (e >> 4)) * es] = v[t];
+            }
         }
     }
     (void)sizeof(real);
@@ -728,6 +768,11 @@ __device__ __forceinline__ void pp_pass_p2_fused2(const C *X0, const C *X1, int 
     const int nb = 1 << lognb;
     const int Ns = 1 << logNs;
     const int total = nbatch << lognb;
+    // (the linear cases of pp_pass_p2 for reads and writes at jj + t nb)
+    const bool xlin = !PADX || nb >= 16 || (nb << LR) <= 16;
+    const bool qlin = !PADQ || nb >= 16 || (nb << LR) <= 16;
+    const int xstep = (PADX ? nb + (nb >> 4) : nb) * xes;
+    const int qstep = (PADQ ? nb + (nb >> 4) : nb) * qes;
     for (int J = tid; J < total; J += nthr) {
         int b, jj;
         if (BFAST) {
@@ -741,12 +786,21 @@ __device__ __forceinline__ void pp_pass_p2_fused2(const C *X0, const C *X1, int 
         const int idxD = ((jj >> logNs) << (logNs + LR)) + k;
         const C *tw = T + k;
         C v0[R], v1[R];
+        if (xlin) {
+            const int a0 = b * xbs + (PADX ? jj + (jj >> 4) : jj) * xes;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const int e = jj + t * nb;
-            const int a = b * xbs + (PADX ? e + (e >> 4) : e) * xes;
-            v0[t] = X0[a];
-            v1[t] = two ? X1[a] : C{0, 0};
+            for (int t = 0; t < R; ++t) {
+                v0[t] = X0[a0 + t * xstep];
+                v1[t] = two ? X1[a0 + t * xstep] : C{0, 0};
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = jj + t * nb;
+                const int a = b * xbs + (e + (e >> 4)) * xes;
+                v0[t] = X0[a];
+                v1[t] = two ? X1[a] : C{0, 0};
+            }
         }
         if (Ns > 1) {
 #pragma unroll
@@ -765,10 +819,16 @@ __device__ __forceinline__ void pp_pass_p2_fused2(const C *X0, const C *X1, int 
 #pragma unroll
             for (int t = 1; t < R; ++t) v0[t] = cmul(v0[t], cconj(tw[t * Ns]));
         }
+        if (qlin) {
+            C *q = Q + b * qbs + (PADQ ? jj + (jj >> 4) : jj) * qes;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const int e = jj + t * nb;
-            Q[b * qbs + (PADQ ? e + (e >> 4) : e) * qes] = v0[t];
+            for (int t = 0; t < R; ++t) q[t * qstep] = v0[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int e = jj + t * nb;
+                Q[b * qbs + (e + (e >> 4)) * qes] = v0[t];
+            }
         }
     }
 }
