@@ -31,15 +31,9 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a
 #ifndef FFTLB_NO_PACKED_F32X2
 // fp32 complex add / subtract as one packed FP32x2 instruction (sm_100+)
 template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
-#ifdef FFTLB_CSUB_FFMA2
-template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
-    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);   // a - b, one rounding
-}
-#else
 template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
     return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
-#endif
 #endif
 // i * a and -i * a
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return C{-a.y, a.x}; }
