@@ -300,12 +300,13 @@ def _droplet512_oracle():
     return fields, kw, O.run(O.init_equilibrium(*fields, p), p, 1)
 
 
-@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("precision", [64, 32, 32 | 256])   # 256: FFTLB_BF16SPLIT
 def test_droplet_512_precision_config(fl, precision):
     """The precision configuration's droplet (512^2, R = 80, Maxwell
     densities at T = 0.8 T_c, tanh width 2), one SSP-RK3 step, element by
     element against the oracle: fp64 within 1e-9, fp32 within
-    fp32_force_bound."""
+    fp32_force_bound, fp32 with the split-BF16 first passes within the same
+    bound with their rounding."""
     fields, kw, f_o = _droplet512_oracle()
     with fl.Handle(fl.params(integrator=3, precision=precision, **kw)) as h:
         h.set_fields(*fields)
@@ -314,7 +315,9 @@ def test_droplet_512_precision_config(fl, precision):
     if precision == 64:
         assert rel_err(f_g, f_o) < 1e-9
     else:
-        bound = fp32_force_bound(512, 1, fields[0], fields[3])
+        split = precision & fl.BF16SPLIT
+        bound = fp32_force_bound(512, 1, fields[0], fields[3], u_split=U_SPLIT if split else 0.0)
         err = (np.abs(f_g - f_o) / np.abs(f_o)).max()
-        print(f"fp32 512^2 droplet after 1 RK3 step: max |df|/f = {err:.3e} (bound {bound:.3e})")
+        name = "split-BF16" if split else "fp32"
+        print(f"{name} 512^2 droplet after 1 RK3 step: max |df|/f = {err:.3e} (bound {bound:.3e})")
         assert err < bound
