@@ -1123,7 +1123,7 @@ class EngineT : public Engine {
     }
 
     Status configure() {
-        const size_t cs = sizeof(C), rs = sizeof(real);
+        const size_t cs = sizeof(C);
         int dev = 0;
         FFTLB_CU(cudaGetDevice(&dev));
         int maxsm = 0;

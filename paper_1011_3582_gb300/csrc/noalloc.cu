@@ -45,6 +45,7 @@ constexpr size_t kOffWc = kOffWp + align32(kMaxLen);                     // kMax
 constexpr size_t kOffGrp = kOffWc + align32(2 * kMaxLen);                // one GroupDesc
 constexpr size_t kTotalDoubles = kOffGrp + align32((sizeof(GroupDesc) + 7) / 8);
 constexpr size_t kStaticBytes = kTotalDoubles * sizeof(double);
+static_assert(kStaticBytes < 2 * 1024 * 1024, "static scratch stays below 2 MB");
 
 static __device__ __align__(256) double g_static_scratch[kTotalDoubles];
 

@@ -300,6 +300,41 @@ def _droplet512_oracle():
     return fields, kw, O.run(O.init_equilibrium(*fields, p), p, 1)
 
 
+@functools.lru_cache(maxsize=None)
+def _bench_workload_oracle():
+    """One SSP-RK3 step of the benchmark workload at full size: 1024^2
+    spinodal quench, rho = rho_c (1 + 0.01 N(0, 1)) seed 7, u = 0,
+    T = 0.7 T_c, a = 9/49, b = 2/21, window k4 (about 15 s of numpy)."""
+    n = 1024
+    fields = W.spinodal(n, n, RHOC49, 0.7 * TC49, amp=0.01, seed=7)
+    kw = dict(nx=n, ny=n, a=A49, b=B21, window=4)
+    p = oracle_params(kw, integrator=3)
+    return fields, kw, O.run(O.init_equilibrium(*fields, p), p, 1)
+
+
+@pytest.mark.parametrize("precision", [32, 64, 32 | 256])   # 256: FFTLB_BF16SPLIT
+def test_bench_workload_1024_full_size(fl, precision):
+    """The benchmarked configuration itself: 1024^2, the launch parameters
+    chosen by fftlb_autotune (as bench.py times it), one SSP-RK3 step,
+    every element of f against the oracle: fp64 within 1e-9, fp32 (and the
+    split-BF16 first passes) within fp32_force_bound."""
+    fields, kw, f_o = _bench_workload_oracle()
+    with fl.Handle(fl.params(integrator=3, precision=precision, **kw)) as h:
+        h.set_fields(*fields)
+        h.autotune()
+        h.step(1)
+        f_g = h.get_f()
+    if precision == 64:
+        assert rel_err(f_g, f_o) < 1e-9
+    else:
+        split = precision & fl.BF16SPLIT
+        bound = fp32_force_bound(1024, 1, fields[0], fields[3], u_split=U_SPLIT if split else 0.0)
+        err = (np.abs(f_g - f_o) / np.abs(f_o)).max()
+        print(f"{'split-BF16' if split else 'fp32'} 1024^2 bench workload, 1 RK3 step: max |df|/f = {err:.3e} "
+              f"(bound {bound:.3e})")
+        assert err < bound
+
+
 @pytest.mark.parametrize("precision", [64, 32, 32 | 256])   # 256: FFTLB_BF16SPLIT
 def test_droplet_512_precision_config(fl, precision):
     """The precision configuration's droplet (512^2, R = 80, Maxwell
