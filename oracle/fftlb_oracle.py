@@ -29,11 +29,12 @@ Pins (tests/test_oracle_*.py, marker "not gpu"):
   * B, Lambda, P^w (Eqs. 18, 19, 21): the exact square-gradient planar profile
     is in mechanical equilibrium (tests/test_oracle_physics.py);
   * C_q (Eq. 23): the entropy mode decays with diffusivity T (tau - q), the
-    Prandtl relation Pr = tau / 2(tau - q) of Sec. 2.2.
+    Prandtl relation Pr = tau / 2(tau - q) of Sec. 2.2;
+  * the zeta terms of B (Eq. 21): a sound wave decays faster by
+    zeta k^2 / 2 rho, the bulk viscosity of the dissipative tensor of
+    Eqs. 13-14 (tests/test_oracle_physics.py).
 Parity unpinned: the term -rho T d_gamma rho d_gamma(M/T) of Eq. 19 (it
-vanishes at uniform T, and total energy is blind to any symmetric Lambda),
-and the sign of the bulk-viscosity (zeta) terms of Eqs. 21-22 (only their
-mutual energy consistency is checked; every workload has zeta = 0).
+vanishes at uniform T, and total energy is blind to any symmetric Lambda).
 """
 from __future__ import annotations
 
