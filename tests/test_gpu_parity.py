@@ -141,6 +141,24 @@ def test_unstable_state_is_reported_not_trapped(fl):
         assert ei.value.steps_done == 1
 
 
+@pytest.mark.parametrize("extra", [dict(zeta=2e-3), dict(H=5e-5), dict(zeta=1e-3, H=-3e-5, q=0.0)])
+def test_bulk_viscosity_and_temperature_dependent_M_fp64(fl, extra):
+    """zeta (the bulk-viscosity terms of Eqs. 21-22) and H (M = K + H T in
+    Eq. 19, which brings in the -rho T d rho . d(M/T) term) off their zero
+    defaults, on smooth non-uniform rho, u and T: fp64 against the oracle
+    after 10 RK3 steps, 1e-9."""
+    n = 32
+    fields = W.smooth_random(n, n, seed=17, rho0=1.2, T0=0.9, amp=0.05, umax=0.02)
+    kw = dict(nx=n, ny=n, dx=1 / 64, K=1e-4, **extra)
+    p = oracle_params(kw, integrator=3)
+    f_o = O.run(O.init_equilibrium(*fields, p), p, 10)
+    with fl.Handle(fl.params(precision=64, integrator=3, **kw)) as h:
+        h.set_fields(*fields)
+        h.step(10)
+        f_g = h.get_f()
+    assert rel_err(f_g, f_o) < 1e-9
+
+
 # a velocity set other than the paper's (1, 1.9, 2.9, 4.3)
 SPEEDS_B = (1.0, 2.0, 3.0, 4.5)
 
