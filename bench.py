@@ -45,6 +45,14 @@ def workload_fields(n, seed=7):
     return workloads.spinodal(n, n, RHOC, 0.7 * TC, amp=0.01, seed=seed)
 
 
+def workload_config(n):
+    """The workload's description, shared by both arms' JSON lines."""
+    return {"workload": "spinodal decomposition %dx%d, rho = rho_c (1 + 0.01 N(0,1)) seed 7, T = 0.7 T_c, "
+                        "vdW a = 9/49 b = 2/21" % (n, n),
+            "grid": n, "integrator": "ssp-rk3", "window": "k4", "dx": 1 / 256, "dt": 1e-5, "tau": 1e-2,
+            "K": 1e-5, "q": -0.004}
+
+
 def workload_params(fl, n, precision, integrator=3):
     return fl.params(nx=n, ny=n, a=A, b=B, precision=precision, integrator=integrator, window=4)
 
@@ -233,10 +241,10 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3.0 * el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "spinodal %dx%d sample of the 1024x1024 workload" % (n, n),
-                                             "grid": n, "integrator": "ssp-rk3", "window": "k4"},
+            "data": "synthetic", "config": workload_config(args.grid),
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d SSP-RK3 stages of a %dx%d sample" % (args.steps, n, n)},
+                             "sample": "%d SSP-RK3 stages (one per timed step) of a %dx%d instance of the same "
+                                       "workload (same generator, seed and parameters)" % (args.steps, n, n)},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -497,17 +505,14 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
-                "config": {"workload": "spinodal decomposition %dx%d, rho = rho_c (1 + 0.01 N(0,1)) seed 7, "
-                                       "T = 0.7 T_c, vdW a = 9/49 b = 2/21" % (n, n),
-                           "grid": n, "integrator": "ssp-rk3", "window": "k4", "dx": 1 / 256, "dt": 1e-5,
-                           "tau": 1e-2, "K": 1e-5, "q": -0.004,
-                           "l2": "inputs larger than L2 (state %.0f MB + spectra %.0f MB)" % (
+                "config": dict(workload_config(n),
+                           l2="inputs larger than L2 (state %.0f MB + spectra %.0f MB)" % (
                                33 * n * n * args.precision / 8 / 1e6, 58 * n * n * args.precision / 8 / 1e6),
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "first_pass": "split-BF16 tensor cores" if prec & 256 else "fp32 radix 16",
-                           "launch_tuning": dict(zip(("tw_conv", "tw_level", "rows_forward", "rows_final",
-                                                      "head_buffers"), tuned[prec]),
-                                                 autotuned=not args.no_autotune)},
+                           parallelism="replicas" if world > 1 else "single",
+                           first_pass="split-BF16 tensor cores" if prec & 256 else "fp32 radix 16",
+                           launch_tuning=dict(zip(("tw_conv", "tw_level", "rows_forward", "rows_final",
+                                                   "head_buffers"), tuned[prec]),
+                                              autotuned=not args.no_autotune)),
                 "roofline": roofline, "kernels": kernels, "alg_bytes_per_step": step_bytes,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": lps * K, "clocks": clocks,
                 "fp64": fp64, "bf16split": bf16split, "sweep": sweep, "cufft_reference": cufft, "invariants_after": inv}
