@@ -353,6 +353,34 @@ def test_bench_workload_1024_full_size(fl, precision):
         assert err < bound
 
 
+def test_max_size_2048_fp32_properties(fl):
+    """The largest fp32 grid (2048^2: eight sites per thread in the row
+    kernels), one SSP-RK3 step with autotuned launch parameters, checked by
+    properties that hold at any size: translation equivariance (a field
+    shifted by (37, 1001) sites steps to the shifted result, within twice
+    fp32_force_bound since both runs round independently) and conservation
+    of mass (to fp32 rounding of the state)."""
+    n = 2048
+    fields = W.spinodal(n, n, RHOC49, 0.8 * TC49, amp=0.01, seed=5)
+    kw = dict(nx=n, ny=n, a=A49, b=B21)
+    shift = (37, 1001)
+    out = []
+    for fl_in in (fields, tuple(np.roll(x, shift, axis=(0, 1)) for x in fields)):
+        with fl.Handle(fl.params(integrator=3, precision=32, **kw)) as h:
+            h.set_fields(*fl_in)
+            h.autotune()
+            m0 = h.invariants()["mass"]
+            h.step(1)
+            out.append(h.get_f())
+            m1 = h.invariants()["mass"]
+        assert abs(m1 - m0) < 1e-6 * m0
+    f_a = np.roll(out[0], shift, axis=(1, 2))
+    err = (np.abs(out[1] - f_a) / np.abs(f_a)).max()
+    bound = 2 * fp32_force_bound(n, 1, fields[0], fields[3])
+    print(f"fp32 2048^2 shifted vs unshifted after 1 RK3 step: max |df|/f = {err:.3e} (bound {bound:.3e})")
+    assert err < bound
+
+
 @pytest.mark.parametrize("precision", [64, 32, 32 | 256])   # 256: FFTLB_BF16SPLIT
 def test_droplet_512_precision_config(fl, precision):
     """The precision configuration's droplet (512^2, R = 80, Maxwell
