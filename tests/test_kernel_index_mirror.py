@@ -11,8 +11,9 @@ The checks:
     compute the DFT, for every power-of-two length to 1024, both batch
     orders and every padding of source and destination;
   * the adjoint passes in reverse order (pp_pass_p2_adj) give n times the
-    inverse DFT, and forward + diagonal multiply + adjoint (the fused
-    column path, pp_conv_p2) gives n IDFT(m DFT(x));
+    inverse DFT: forward + diagonal multiply + adjoint gives n IDFT(m DFT(x)),
+    also with the last forward pass, the multiply and its adjoint fused in
+    registers (pp_pass_p2_fused, the convection columns of pp_conv_p2);
   * the constant-stride addresses the passes use instead of padding each
     index (base + t (S + S/16), or base + t S inside one 16-element block)
     equal the padded indices wherever the code takes them;
@@ -185,6 +186,54 @@ def test_adjoint_passes_and_fused_multiply(n):
         where ^= 1
     got = unload(bufs[where], lays[where], n, nbatch)
     want = n * np.fft.ifft(m[None, :] * np.fft.fft(x, axis=1), axis=1)
+    assert np.abs(got - want).max() < 1e-9 * n
+
+
+def fused_pass(buf, lay, logn, nbatch, lr, lns, T, mult, bfast):
+    """pp_pass_p2_fused: the last forward pass, the multiply of output
+    element idxD + t Ns of transform b, and its adjoint, in registers, read
+    from and written back to the same positions jj + t nb."""
+    R, lognb, Ns = 1 << lr, logn - lr, 1 << lns
+    nb = 1 << lognb
+    bs, es, p = lay
+    Wf = np.exp(-2j * np.pi * np.outer(np.arange(R), np.arange(R)) / R)
+    for J in range(nbatch << lognb):
+        b, jj = decompose(J, nbatch, lognb, bfast)
+        k = jj & (Ns - 1)
+        idxD = ((jj >> lns) << (lns + lr)) + k
+        addrs = [b * bs + a * es for a in read_addrs(jj, nb, R, p)]
+        v = buf[addrs].copy()
+        tw = np.array([T[t * Ns + k] for t in range(R)]) if Ns > 1 else np.ones(R)
+        v = Wf @ (v * tw)
+        v = v * np.array([mult(b, idxD + t * Ns) for t in range(R)])
+        v = np.conj(tw) * (np.conj(Wf) @ v)
+        buf[addrs] = v
+
+
+@pytest.mark.parametrize("n", [4, 32, 256, 1024])
+def test_fused_last_pass(n):
+    """Forward passes 1 .. L-1, the fused pass L, adjoint passes L-1 .. 1
+    (pp_conv_p2): n IDFT(m DFT(x)) with 2L - 1 passes."""
+    rng = np.random.default_rng(n + 1)
+    nbatch = 4 if n <= 256 else 1
+    logn = n.bit_length() - 1
+    x = rng.standard_normal((nbatch, n)) + 1j * rng.standard_normal((nbatch, n))
+    m = rng.standard_normal((nbatch, n)) + 1j * rng.standard_normal((nbatch, n))
+    T = tables(n)
+    lays = [layout(n, nbatch, 0, True), layout(n, nbatch, 1, True)]
+    bufs = [load(x, lays[0], n, nbatch), load(np.zeros_like(x), lays[1], n, nbatch)]
+    sched = schedule(logn)
+    where = 0
+    for lr, lns, off in sched[:-1]:
+        fwd_pass(bufs[where], bufs[where ^ 1], lays[where], lays[where ^ 1], logn, nbatch, lr, lns, T[off:], True)
+        where ^= 1
+    lr, lns, off = sched[-1]
+    fused_pass(bufs[where], lays[where], logn, nbatch, lr, lns, T[off:], lambda b, e: m[b, e], True)
+    for lr, lns, off in reversed(sched[:-1]):
+        adj_pass(bufs[where], bufs[where ^ 1], lays[where], lays[where ^ 1], logn, nbatch, lr, lns, T[off:], True)
+        where ^= 1
+    got = unload(bufs[where], lays[where], n, nbatch)
+    want = n * np.fft.ifft(m * np.fft.fft(x, axis=1), axis=1)
     assert np.abs(got - want).max() < 1e-9 * n
 
 
