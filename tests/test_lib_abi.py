@@ -98,3 +98,49 @@ def test_cnn_parameter_packing_round_trip(fl):
     back = fl.unpack_params(vec.astype(np.float64))
     for (W1, b1), (W2, b2) in zip(params, back):
         assert np.allclose(W1, W2, rtol=1e-6, atol=1e-7) and np.allclose(b1, b2)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "fftlb.h"
+#include "fftlb_warmstart.h"
+
+int main(void) {
+    fftlb_params p;
+    memset(&p, 0, sizeof p);
+    p.nx = 10; p.ny = 16; p.dx = 1.0 / 256; p.dt = 1e-5; p.tau = 1e-2;
+    p.a = 9.0 / 8; p.b = 1.0 / 3; p.K = 1e-5; p.q = -0.004;
+    p.window = 4; p.integrator = 3; p.precision = 32 | FFTLB_BF16SPLIT;
+    fftlb_t h = (fftlb_t)1;
+    fftlb_status st = fftlb_create(&h, &p, NULL, NULL);
+    const char *msg = fftlb_last_error(NULL);   /* valid until the next call */
+    if (st != FFTLB_ERR_ARG || h != NULL || msg == NULL || strlen(msg) < 10) return 1;
+    printf("%s\n", msg);
+    fftlb_cnn_t c = (fftlb_cnn_t)1;
+    if (fftlb_cnn_create(&c, 8, 100, NULL) != FFTLB_ERR_ARG) return 2;
+    return 0;
+}
+"""
+
+
+def test_plain_c_client_compiles_links_and_gets_argument_errors(fl, tmp_path):
+    """The boundary is a C ABI: a C99 program includes both headers, links
+    libfftlb.so and gets FFTLB_ERR_ARG with a message for an invalid grid
+    (the checks come before any device work, so no GPU is needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(fl.LIB_PATH)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-lfftlb", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert "nx" in run.stdout
