@@ -210,16 +210,16 @@ class ClockSampler:
 
 
 def cpu_baseline(n=1024):
-    """The FP64 oracle on the host: one SSP-RK3 stage of the n x n workload
-    (a third of a step), scaled to MLUPS per full step."""
+    """The FP64 oracle on the host: one SSP-RK3 step of the n x n workload
+    (about 15 s of one core at 1024^2)."""
     from oracle import fftlb_oracle as O
     p = O.Params(nx=n, ny=n, a=A, b=B, integrator=3, window=4)
     f = O.init_equilibrium(*workload_fields(n), p)
     t0 = time.perf_counter()
-    f = f + p.dt * O.rhs(f, p)
+    f = O.step(f, p)
     dt = time.perf_counter() - t0
-    return {"value": n * n / (3.0 * dt) / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "one SSP-RK3 stage of the %dx%d workload (1/3 step), numpy fp64, %.1f s" % (n, n, dt)}
+    return {"value": n * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "one SSP-RK3 step of the %dx%d workload, numpy fp64, %.1f s" % (n, n, dt)}
 
 
 def run_reference(args, rank, world):
