@@ -32,9 +32,11 @@ Pins (tests/test_oracle_*.py, marker "not gpu"):
     Prandtl relation Pr = tau / 2(tau - q) of Sec. 2.2;
   * the zeta terms of B (Eq. 21): a sound wave decays faster by
     zeta k^2 / 2 rho, the bulk viscosity of the dissipative tensor of
-    Eqs. 13-14 (tests/test_oracle_physics.py).
-Parity unpinned: the term -rho T d_gamma rho d_gamma(M/T) of Eq. 19 (it
-vanishes at uniform T, and total energy is blind to any symmetric Lambda).
+    Eqs. 13-14 (tests/test_oracle_physics.py);
+  * Lambda at non-uniform T, including -rho T d_gamma rho d_gamma(M/T) of
+    Eq. 19: at f = f^eq with q = zeta = 0 the rates conserve the vdW entropy
+    plus the -(H/2)|grad rho|^2 gradient entropy (tests/test_oracle_entropy.py).
+Parity unpinned: none.
 """
 from __future__ import annotations
 
