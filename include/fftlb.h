@@ -175,6 +175,21 @@ const char *fftlb_kernel_name(int kind);
 fftlb_status fftlb_autotune(fftlb_t h, double *stage_ms);
 fftlb_status fftlb_tuning(fftlb_t h, int tuning[5], int set);
 
+/* Test hook of the bounded device waits; the paper has no counterpart.  The
+ * pipelined kernels wait for their staged copies on shared-memory barriers,
+ * and every such wait gives up after a time limit (2 s), records a bit in the
+ * handle's device error word and lets its block return, so that a stuck copy
+ * cannot hang the GPU.  With ns > 0 (1e3 <= ns <= 1e9), every later stage
+ * first launches one small kernel whose blocks wait, with the same code and
+ * a limit of ns nanoseconds, on a barrier that nothing ever completes (no
+ * copy is issued there); the wait runs out and sets the error word.  The
+ * next call that reads the word (fftlb_step with check_every > 0,
+ * fftlb_fields, fftlb_invariants) returns FFTLB_ERR_TIMEOUT, and every later
+ * one does too: the word is not cleared, so the handle should be destroyed
+ * (which works as usual).  ns = 0 turns the hook off.  FFTLB_ERR_ARG for
+ * other values. */
+fftlb_status fftlb_debug_wait_test(fftlb_t h, long long ns);
+
 /* Batched sweep: nruns independent problems (each its own grid, parameters
  * and state; the same velocity set) advanced together.  Runs with identical
  * fftlb_params (check_every aside) form a group whose states are stored
@@ -216,9 +231,11 @@ const char *fftlb_batch_last_error(fftlb_batch_t b);
  * loads it until the process exits.
  *  - Limits: nx, ny even 2^p 3^q in [4, 1024] and nx * ny <= 65536; larger
  *    grids return FFTLB_ERR_ARG with a message (fftlb_last_error(NULL)).
- *  - The first call on a device looks up the array's device address and
- *    sets a kernel attribute (once per device, with that device current);
- *    make that first call before any stream capture.
+ *  - Every call looks up the array's device address and sets a kernel
+ *    attribute, with the caller's device current (neither allocates), so a
+ *    device reset between calls is harmless.  The first call on a device
+ *    may also load the library's module there: make that first call before
+ *    any stream capture.
  *  - Every call shares the one array, which keeps the last call's contents:
  *    calls that overlap on the GPU (several streams or host threads) race
  *    and give wrong results.  Serialise them.

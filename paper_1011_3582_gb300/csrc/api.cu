@@ -200,6 +200,12 @@ fftlb_status fftlb_tuning(fftlb_t h, int tuning[5], int set) {
     return st.good() ? FFTLB_OK : fail(h, st);
 }
 
+fftlb_status fftlb_debug_wait_test(fftlb_t h, long long ns) {
+    if (!h) return fail(nullptr, FFTLB_ERR_ARG, "NULL handle");
+    fftlb::Status st = h->eng->set_wait_test(ns);
+    return st.good() ? FFTLB_OK : fail(h, st);
+}
+
 const char *fftlb_kernel_name(int kind) {
     return (kind >= 0 && kind < fftlb::KK_COUNT) ? fftlb::kKernelNames[kind] : "";
 }

@@ -60,21 +60,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// bounded wait by this thread; false if the phase did not complete
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// bounded wait by this thread; false if the phase did not complete within
+// limit_ns of %globaltimer time (or kWaitPolls polls)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned i = 1; i < kWaitPolls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+        if ((i & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
 
 // Block-wide wait for one phase.  Returns false in every thread if any
 // thread gave up; the caller then records the error and drains.
-__device__ __forceinline__ bool block_wait(uint64_t *bar, uint32_t parity, int *err) {
-    const bool ok = mbar_wait_bounded(bar, parity);
+__device__ __forceinline__ bool block_wait(uint64_t *bar, uint32_t parity, int *err,
+                                           unsigned long long limit_ns = kWaitNs) {
+    const bool ok = mbar_wait_bounded(bar, parity, limit_ns);
     const int bad = __syncthreads_or(ok ? 0 : 1);
     if (bad && threadIdx.x == 0) atomicOr(err, kErrWaitTimeout);
     return bad == 0;

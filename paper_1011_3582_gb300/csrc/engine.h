@@ -60,6 +60,9 @@ class Engine {
     // times candidate parameters on the current state (saved and restored)
     // and keeps the fastest; *stage_ms receives the best stage time
     virtual Status autotune(double *stage_ms) = 0;
+    // test hook of the bounded device waits: ns > 0 makes every stage start
+    // with a kernel whose wait nothing completes (limit ns); 0 turns it off
+    virtual Status set_wait_test(long long ns) = 0;
 };
 
 // kernel kinds of one stage (index into the profile arrays)

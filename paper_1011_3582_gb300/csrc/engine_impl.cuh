@@ -629,12 +629,26 @@ class EngineT : public Engine {
     Status gradient(const double *g, double *out, int nfields) override {
         if (!g || !out || nfields < 1 || nfields > 16)
             return Status::err(FFTLB_ERR_ARG, "gradient: need device pointers and 1 <= nfields <= 16");
-        k_rows_forward<real, double><<<dim3(ny_, nfields), NT, smem_rows1_, stream_>>>(g, spec_, 0, Wr_, Wp_, kp_);
-        FFTLB_LAUNCHED("k_rows_forward");
-        Status st = run_groups(grad_groups_ + 0, nfields, 1);
+        // the stage's transform code (and, for split handles, its split-BF16
+        // first passes); field i in slot i -> D_x, D_y in slots 20 + 2i, 21 + 2i
+        Status st = grad_config();
         if (!st.good()) return st;
-        k_rows_inverse<real, double><<<dim3(ny_, 2 * nfields), NT, smem_rows1_, stream_>>>(spec_, 20, out, Wr_, Wp_, kp_);
-        FFTLB_LAUNCHED("k_rows_inverse");
+        k_grad_rows_fwd<real, split_><<<dim3(ny_, nfields), NT3, smem_gr_, stream_>>>(g, spec_, 0, Wr_, Wp_, Tr_,
+                                                                                      ntr_, kp_);
+        FFTLB_LAUNCHED("k_grad_rows_fwd");
+        k_grad_col<real, split_><<<dim3(h_ / TWg_, nfields), NT3, smem_gc_, stream_>>>(
+            spec_, groups_ + grad_groups_, kxt_, kyt_, Wc_, Tc_, ntc_, kp_, TWg_);
+        FFTLB_LAUNCHED("k_grad_col");
+        k_grad_rows_inv<real, split_><<<dim3(ny_, 2 * nfields), NT3, smem_gr_, stream_>>>(spec_, 20, out, Wr_, Wp_,
+                                                                                          Tr_, ntr_, kp_);
+        FFTLB_LAUNCHED("k_grad_rows_inv");
+        return Status::ok();
+    }
+
+    Status set_wait_test(long long ns) override {
+        if (ns != 0 && (ns < 1000 || ns > 1000000000LL))
+            return Status::err(FFTLB_ERR_ARG, "wait test limit must be 0 or in [1e3, 1e9] ns");
+        wait_test_ns_ = (unsigned long long)ns;
         return Status::ok();
     }
 
@@ -678,6 +692,11 @@ class EngineT : public Engine {
     std::vector<void *> allocs_;
     // group ranges in groups_
     int conv_groups_ = 0, l1_groups_ = 0, l2_groups_ = 0, grad_groups_ = 0, inv_groups_ = 0;
+    // gradient kernels (k_grad_*): column tile width and shared memory
+    int TWg_ = 0;
+    size_t smem_gr_ = 0, smem_gc_ = 0;
+    // test hook: nonzero = every stage starts with k_wait_selftest (ns)
+    unsigned long long wait_test_ns_ = 0;
     // launch configuration
     int TW_ = 1;
     size_t smem_col1_ = 0, smem_col2_ = 0, smem_rows1_ = 0, smem_inv_ = 0;
@@ -1398,6 +1417,28 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
+    // shared memory and tile width of the gradient kernels (first use)
+    Status grad_config() {
+        if (TWg_) return Status::ok();
+        const size_t cs = sizeof(C), pny = (size_t)padded_len(ny_);
+        smem_gr_ = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, h_ * cs, (size_t)padded_len(h_) * cs});
+        int tw = 0;
+        for (int t = 8; t >= 1; t >>= 1) {
+            if (h_ % t) continue;
+            const size_t sm = smem_bytes({ny_ * cs, ntc_ * cs, (size_t)t * ny_ * cs, t * pny * cs, t * pny * cs});
+            if (sm > budget_) continue;
+            tw = t;
+            smem_gc_ = sm;
+            break;
+        }
+        if (!tw || smem_gr_ > budget_) return Status::err(FFTLB_ERR_ARG, "grid too large for the gradient kernels");
+        FFTLB_CU(cudaFuncSetAttribute(k_grad_rows_fwd<real, split_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
+        FFTLB_CU(cudaFuncSetAttribute(k_grad_rows_inv<real, split_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
+        FFTLB_CU(cudaFuncSetAttribute(k_grad_col<real, split_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
+        TWg_ = tw;
+        return Status::ok();
+    }
+
     Status run_groups(int first, int count, int nin_max) {
         const size_t sm = nin_max == 1 ? smem_col1_ : smem_col2_;
         k_col<real><<<dim3(h_ / TW_, count), NT, sm, stream_>>>(spec_, groups_ + first, kxt_, kyt_, Wc_, kp_, TW_,
@@ -1571,6 +1612,10 @@ class EngineT : public Engine {
 
     Status stage(const real *cur, const real *base, real *out, real alpha, real beta) {
         Status st;
+        if (wait_test_ns_) {
+            k_wait_selftest<<<nsm_, 128, 0, stream_>>>(err_, wait_test_ns_);
+            FFTLB_LAUNCHED("k_wait_selftest");
+        }
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
         if (SMAX1_ == 1)
             k1_pipe<real, 1, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,

@@ -1014,4 +1014,151 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
     }
 }
 
+// ---------------------------------------------------------------------------
+// Spectral gradient of caller fields (fftlb_gradient) through the stage's
+// transform code: pp_fft_any (shift-based passes for power-of-two lengths,
+// radix 16 first) and, when TC is set, the split-BF16 tensor-core first
+// pass of every row and column transform.  One row or one column tile per
+// block; not pipelined (the gradient is not on the stepping path).
+// ---------------------------------------------------------------------------
+
+// forward rows of nf real fields [nf][ny][nx] into slots slot0 + fi
+template <typename real, bool TC = false>
+__global__ void __launch_bounds__(NT3) k_grad_rows_fwd(const double *__restrict__ in,
+                                                       typename cplx_of<real>::type *spec, int slot0,
+                                                       const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                       const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                       const typename cplx_of<real>::type *__restrict__ Tr_g, int ntr,
+                                                       KP<real> P) {
+    using C = typename cplx_of<real>::type;
+    const uint4 *tc = TC ? P.tc16 : nullptr;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, fi = blockIdx.y, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    SmemCursor sc{smem_raw, 0u};
+    C *Wr = (C *)sc.take(h * sizeof(C));
+    C *Wp = (C *)sc.take(h * sizeof(C));
+    C *Tr = (C *)sc.take(ntr * sizeof(C));
+    C *buf = (C *)sc.take(h * sizeof(C));
+    C *wk = (C *)sc.take(padded_len(h) * sizeof(C));
+    const Lay la{h, 1, 0}, lb{padded_len(h), 1, 1};
+    load_tab(Wr, Wr_g, h, NT3);
+    load_tab(Wp, Wp_g, h, NT3);
+    load_tab(Tr, Tr_g, ntr, NT3);
+    real *bre = reinterpret_cast<real *>(buf);
+    for (int x = tid; x < nx; x += NT3) bre[x] = (real)in[(size_t)fi * N + (size_t)y * nx + x];
+    __syncthreads();
+    const int w = pp_fft_any<-1, false, 0, 1>(buf, la, wk, lb, h, 1, Wr, Tr, tid, NT3, 4, tc);
+    C *res = w ? wk : buf;
+    const Lay lr = w ? lb : la;
+    r2c_post_l(res, lr, h, 1, Wp, tid, NT3);
+    __syncthreads();
+    C *dst = spec + (size_t)(slot0 + fi) * slot + (size_t)y * h;
+    for (int k = tid; k < h; k += NT3) dst[k] = res[lr(0, k)];
+}
+
+// column tile blockIdx.x of group blockIdx.y (one input): forward, then per
+// output the multiplier into a free buffer and the inverse
+template <typename real, bool TC = false>
+__global__ void __launch_bounds__(NT3) k_grad_col(typename cplx_of<real>::type *spec,
+                                                  const GroupDesc *__restrict__ groups,
+                                                  const real *__restrict__ kxt, const real *__restrict__ kyt,
+                                                  const typename cplx_of<real>::type *__restrict__ Wc_g,
+                                                  const typename cplx_of<real>::type *__restrict__ Tc_g, int ntc,
+                                                  KP<real> P, int TW) {
+    using C = typename cplx_of<real>::type;
+    const uint4 *tc = TC ? P.tc16 : nullptr;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ GroupDesc gd;
+    const int ny = P.ny, h = P.h, tid = threadIdx.x;
+    const size_t slot = (size_t)ny * h;
+    const int kx0 = blockIdx.x * TW, lgTW = ilog2(TW);
+    const int pny = padded_len(ny);
+    SmemCursor sc{smem_raw, 0u};
+    C *Wc = (C *)sc.take(ny * sizeof(C));
+    C *Tc = (C *)sc.take(ntc * sizeof(C));
+    C *A = (C *)sc.take((size_t)TW * ny * sizeof(C));     // unpadded [c][ny]
+    C *B = (C *)sc.take((size_t)TW * pny * sizeof(C));    // padded
+    C *D = (C *)sc.take((size_t)TW * pny * sizeof(C));    // padded
+    const Lay la{ny, 1, 0}, lb{pny, 1, 1};
+    if (tid == 0) gd = groups[blockIdx.y];
+    load_tab(Wc, Wc_g, ny, NT3);
+    load_tab(Tc, Tc_g, ntc, NT3);
+    __syncthreads();
+    const C *src = spec + (size_t)gd.in_slot[0] * slot;
+    for (int idx = tid; idx < TW * ny; idx += NT3) {
+        const int c = idx & (TW - 1), e = idx >> lgTW;
+        A[la(c, e)] = src[(size_t)e * h + kx0 + c];
+    }
+    __syncthreads();
+    const int w = pp_fft_any<-1, false, 0, 1>(A, la, B, lb, ny, TW, Wc, Tc, tid, NT3, 4, tc);
+    C *X = w ? B : A;
+    const Lay lx = w ? lb : la;
+    for (int o = 0; o < gd.nout; ++o) {
+        C *F = w ? A : B;   // the buffer X does not use
+        const Lay lf = w ? la : lb;
+        col_multiply<real>(F, lf, X, lx, X, lx, gd, o, kxt, kyt, kx0, TW, lgTW, ny, h, P.scale, NT3);
+        __syncthreads();
+        const int w2 = lf.pad ? pp_fft_any<+1, false, 1, 1>(F, lf, D, lb, ny, TW, Wc, Tc, tid, NT3, 4, tc)
+                              : pp_fft_any<+1, false, 0, 1>(F, lf, D, lb, ny, TW, Wc, Tc, tid, NT3, 4, tc);
+        const C *R = w2 ? D : F;
+        const Lay lr = w2 ? lb : lf;
+        C *dst = spec + (size_t)gd.out_slot[o] * slot;
+        for (int idx = tid; idx < TW * ny; idx += NT3) {
+            const int c = idx & (TW - 1), e = idx >> lgTW;
+            dst[(size_t)e * h + kx0 + c] = R[lr(c, e)];
+        }
+        __syncthreads();
+    }
+}
+
+// inverse rows of slots slot0 + fi into real fields out[fi][ny][nx]
+template <typename real, bool TC = false>
+__global__ void __launch_bounds__(NT3) k_grad_rows_inv(const typename cplx_of<real>::type *spec, int slot0,
+                                                       double *__restrict__ out,
+                                                       const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                       const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                       const typename cplx_of<real>::type *__restrict__ Tr_g, int ntr,
+                                                       KP<real> P) {
+    using C = typename cplx_of<real>::type;
+    const uint4 *tc = TC ? P.tc16 : nullptr;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, fi = blockIdx.y, tid = threadIdx.x;
+    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
+    SmemCursor sc{smem_raw, 0u};
+    C *Wr = (C *)sc.take(h * sizeof(C));
+    C *Wp = (C *)sc.take(h * sizeof(C));
+    C *Tr = (C *)sc.take(ntr * sizeof(C));
+    C *buf = (C *)sc.take(h * sizeof(C));
+    C *wk = (C *)sc.take(padded_len(h) * sizeof(C));
+    const Lay la{h, 1, 0}, lb{padded_len(h), 1, 1};
+    load_tab(Wr, Wr_g, h, NT3);
+    load_tab(Wp, Wp_g, h, NT3);
+    load_tab(Tr, Tr_g, ntr, NT3);
+    const C *src = spec + (size_t)(slot0 + fi) * slot + (size_t)y * h;
+    for (int k = tid; k < h; k += NT3) buf[k] = src[k];
+    __syncthreads();
+    c2r_pre_l(buf, la, h, 1, Wp, tid, NT3);
+    __syncthreads();
+    const int w = pp_fft_any<+1, false, 0, 1>(buf, la, wk, lb, h, 1, Wr, Tr, tid, NT3, 4, tc);
+    const C *res = w ? wk : buf;
+    const Lay lr = w ? lb : la;
+    for (int x = tid; x < nx; x += NT3) out[(size_t)fi * N + (size_t)y * nx + x] = (double)real_at<real>(res, lr, 0, x);
+}
+
+// A wait that nothing completes, for testing the bounded-wait error path:
+// every block initialises an mbarrier that expects one arrival, which never
+// comes, and waits on it for at most limit_ns.  The wait runs out,
+// block_wait records kErrWaitTimeout in the device error word and the block
+// returns.  No copy is issued, so nothing is in flight when it returns.
+static __global__ void k_wait_selftest(int *err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    block_wait(&bar, 0, err, limit_ns);
+}
+
 }  // namespace fftlb

@@ -16,8 +16,6 @@
 // All calls share the one array and it keeps the last call's contents:
 // calls that overlap on the GPU (several streams, several host threads)
 // race on it and give wrong results; serialise them.
-#include <mutex>
-
 #include "engine_impl.cuh"
 
 namespace fftlb {
@@ -32,7 +30,6 @@ using fftlb::NT;
 
 constexpr int kMaxLen = 1024;                 // nx, ny limit
 constexpr int kMaxSites = 65536;              // nx * ny limit (e.g. 256 x 256)
-constexpr int kMaxDevices = 64;
 
 // layout of the array, in doubles (each part 256-byte aligned)
 constexpr size_t align32(size_t n) { return (n + 31) & ~size_t(31); }
@@ -49,11 +46,6 @@ static_assert(kStaticBytes < 2 * 1024 * 1024, "static scratch stays below 2 MB")
 
 static __device__ __align__(256) double g_static_scratch[kTotalDoubles];
 
-// per-device address of g_static_scratch (host code may not use the symbol
-// itself as a device address)
-std::mutex g_mu;
-double *g_addr[kMaxDevices] = {nullptr};
-int g_budget[kMaxDevices] = {0};
 
 bool valid_len(int n) {
     if (n < 4 || n > kMaxLen || (n & 1)) return false;
@@ -139,25 +131,24 @@ fftlb_status fail(fftlb_status code, const std::string &msg) {
     return code;
 }
 
-// Once per device, with that device current: the device address of the
-// array and the shared-memory opt-in of the column kernel.
+// With the caller's device current: the device address of the array (host
+// code may not use the symbol itself as a device address) and the
+// shared-memory opt-in of the column kernel.  Both are looked up again on
+// every call: they are cheap, allocate nothing, and stay right after a
+// device reset, which loads the module into a new context (a cached address
+// would then name memory the array no longer occupies).
 fftlb_status setup(int dev, double **addr, int *budget) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) return fail(FFTLB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        int maxsm = 0;
-        e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return fail(FFTLB_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
-        const int budget_b = maxsm - 2048;
-        e = cudaFuncSetAttribute(fftlb::k_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget_b);
-        if (e != cudaSuccess) return fail(FFTLB_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-        g_budget[dev] = budget_b;
-        g_addr[dev] = reinterpret_cast<double *>(p);
-    }
-    *addr = g_addr[dev];
-    *budget = g_budget[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return fail(FFTLB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    int maxsm = 0;
+    e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return fail(FFTLB_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    const int budget_b = maxsm - 2048;
+    e = cudaFuncSetAttribute(fftlb::k_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget_b);
+    if (e != cudaSuccess) return fail(FFTLB_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    *addr = reinterpret_cast<double *>(p);
+    *budget = budget_b;
     return FFTLB_OK;
 }
 
@@ -175,8 +166,7 @@ extern "C" fftlb_status fftlb_gradient_static(const double *g, double *out, int 
         return fail(FFTLB_ERR_ARG, "fftlb_gradient_static: need dx > 0 and window in 0..4");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(FFTLB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(FFTLB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     double *base = nullptr;
     int budget = 0;
     fftlb_status st = setup(dev, &base, &budget);

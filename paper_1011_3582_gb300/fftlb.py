@@ -28,7 +28,7 @@ EXPORTED = ["fftlb_create", "fftlb_set_fields", "fftlb_step", "fftlb_fields", "f
             "fftlb_set_f", "fftlb_invariants", "fftlb_gradient", "fftlb_save", "fftlb_load",
             "fftlb_destroy", "fftlb_last_error", "fftlb_launches_per_step", "fftlb_profile",
             "fftlb_profile_read", "fftlb_kernel_name", "fftlb_gradient_static", "fftlb_autotune",
-            "fftlb_tuning", "fftlb_batch_create", "fftlb_batch_set_fields", "fftlb_batch_step",
+            "fftlb_tuning", "fftlb_debug_wait_test", "fftlb_batch_create", "fftlb_batch_set_fields", "fftlb_batch_step",
             "fftlb_batch_fields", "fftlb_batch_get_f", "fftlb_batch_invariants", "fftlb_batch_tuning",
             "fftlb_batch_launches_per_step", "fftlb_batch_destroy", "fftlb_batch_last_error",
             "fftlb_cnn_create", "fftlb_cnn_destroy", "fftlb_cnn_last_error", "fftlb_cnn_set_params",
@@ -74,6 +74,7 @@ _lib.fftlb_profile_read.argtypes = [_h, ct.POINTER(ct.c_double), ct.POINTER(ct.c
 _lib.fftlb_gradient_static.argtypes = [_p, _p, ct.c_int, ct.c_int, ct.c_double, ct.c_int, _p]
 _lib.fftlb_autotune.argtypes = [_h, ct.POINTER(ct.c_double)]
 _lib.fftlb_tuning.argtypes = [_h, ct.POINTER(ct.c_int), ct.c_int]
+_lib.fftlb_debug_wait_test.argtypes = [_h, ct.c_longlong]
 _lib.fftlb_batch_create.argtypes = [ct.POINTER(_h), ct.c_int, ct.POINTER(fftlb_params), ct.POINTER(fftlb_velset),
                                     ct.c_int, _p]
 _lib.fftlb_batch_set_fields.argtypes = [_h, ct.c_int, _p, _p, _p, _p, ct.c_int]
@@ -235,6 +236,11 @@ class Handle:
         t = (ct.c_int * 5)(*(values or [0] * 5))
         self._check(_lib.fftlb_tuning(self._h, t, 0 if values is None else 1))
         return list(t)
+
+    def debug_wait_test(self, ns):
+        """fftlb_debug_wait_test: every later stage starts with a kernel whose
+        bounded wait nothing completes (limit ns; 0 = off)."""
+        self._check(_lib.fftlb_debug_wait_test(self._h, int(ns)))
 
     def close(self):
         if self._h:

@@ -62,3 +62,28 @@ def gpu_run(fl, name, nsteps, integrator, precision, window=4):
 
 def rel_err(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u_split=0.0):
+    """Elementwise bound on |df_i| / f_i of the FP32 path after nsteps RK3
+    steps.  Two sources: (1) each stage update rounds f_i at most twice, and
+    the initial f^eq once: 4 (S + 1) u with a factor 2 of margin; (2) the
+    force coefficient B (Eq. 21) contains d_b Lambda_ab with Lambda
+    containing K rho lap(rho) (Eq. 19), a third spectral derivative of rho.
+    The rounding of an FP32 transform is spread over all wavenumbers with rms
+    ~ u sqrt(log2 N) rms(rho) (two chained transforms: factor 2), and the
+    third derivative multiplies wavenumber k by |k|^3; over the square
+    spectrum of the window-4 symbol (max k_max = (2/dx)(1 + 1/6 + 3/40 +
+    5/112)) the rms of |k|^3 is 0.83 k_max^3.  |v - u| |dB| dt per stage,
+    over S = 3 nsteps stages, times sqrt(2 ln M) for the maximum over the M
+    values of f, times 2 of margin.  u_split: the relative error of one
+    split-BF16 first pass (the row and the column first passes of a 2-D
+    transform add 2 u_split to its u sqrt(log2 N))."""
+    u, S = 2.0 ** -24, 3 * nsteps
+    N = n * n if np.isscalar(n) else n[0] * n[1]   # n or (ny, nx)
+    kmax = (2 / dx) * (1 + 1 / 6 + 3 / 40 + 5 / 112)
+    eps = (u * np.sqrt(np.log2(N)) + 2 * u_split) * np.sqrt(np.mean(rho ** 2))
+    d3 = 2 * eps * 0.83 * kmax ** 3
+    dB = vmax * K * d3 / T.min()
+    tail = np.sqrt(2 * np.log(33 * N))
+    return 4 * (S + 1) * u + 2 * tail * S * dt * dB

@@ -90,3 +90,23 @@ def test_ncu_traffic_summary_from_a_launch_csv(tmp_path):
         assert sum(res[k]) / 2 == pytest.approx(1000.0 * j + 0.5 + 10.0 * j)
     rows = [ln.split() for ln in out.read_text().splitlines() if not ln.startswith("#")]
     assert {r[0] for r in rows} == set(want) and all(r[1] == "32" and r[2] == "1024" for r in rows)
+
+
+def test_reference_arm_line_describes_what_it_ran(capsys):
+    """The reference arm times full SSP-RK3 steps of the main line's own
+    workload: its config is the main line's, and steps / warmup are the
+    counts it actually ran (capped), so ms_per_step x steps is its timed
+    region."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import json
+    import bench
+    args = argparse.Namespace(steps=20, warmup=5, grid=16)
+    bench.run_reference(args, rank=0, world=1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.workload_config(16)
+    assert line["steps"] == bench.REF_MAX_STEPS and line["warmup"] == 1
+    assert line["steps_requested"] == 20
+    assert line["value"] == pytest.approx(16 * 16 / (line["ms_per_step"] * 1e-3) / 1e6, rel=1e-9)
+    assert line["cpu_baseline"]["value"] == line["value"] and line["e2e"]["value"] == line["value"]

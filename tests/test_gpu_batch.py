@@ -1,10 +1,12 @@
-"""Batched sweep (fftlb_batch_*): runs of uneven grids advanced together by
+"""Batched sweep (fftlb_batch_*): every run of a mixed-shape batch against
+the oracle, element by element; runs of uneven grids advanced together by
 CUDA-graph replays give exactly the results of single handles; the
 autotuner changes launch parameters but not results."""
 import numpy as np
 import pytest
 
-from gpu_common import A49, B21, TC49, lib, rel_err
+from gpu_common import A49, B21, TC49, droplet_ragged, fp32_force_bound, lib, oracle_params, rel_err
+from oracle import fftlb_oracle as O
 from oracle import thermo as TH
 from paper_1011_3582_gb300 import workloads as W
 
@@ -98,3 +100,33 @@ def test_batch_of_euler_runs_matches_single_handles(fl):
             h.set_fields(*fields)
             h.step(5)
             assert np.array_equal(got[r], h.get_f()), r
+
+
+def test_batch_runs_match_oracle(fl):
+    """A batch of uneven grids and both precisions, autotuned per group,
+    compared run by run with the FP64 oracle after 3 SSP-RK3 steps: two
+    64^2 slabs at different temperatures share one group (one launch over
+    both runs), a 48 x 96 droplet has radix-3 axes, and two 128^2 spinodal
+    quenches share an fp32 group beside a 96^2 fp32 slab.  FP64 runs: the
+    1e-9 bar; FP32 runs: fp32_force_bound elementwise."""
+    nsteps = 3
+    drop_fields, drop_kw = droplet_ragged()
+    cases = [slab_case(64, 0.9, 64, 21), slab_case(64, 0.8, 64, 22),
+             (drop_fields, dict(drop_kw, precision=64, integrator=3)),
+             spinodal_case(128, 0.8, 32, 23), spinodal_case(128, 0.75, 32, 24), slab_case(96, 0.85, 32, 25)]
+    with fl.Batch([fl.params(**kw) for _, kw in cases], autotune=True) as b:
+        for r, (fields, _) in enumerate(cases):
+            b.set_fields(r, *fields)
+        b.step(nsteps)
+        got = [b.get_f(r) for r in range(len(cases))]
+    for r, (fields, kw) in enumerate(cases):
+        p = oracle_params(kw)
+        f_o = O.run(O.init_equilibrium(*fields, p), p, nsteps)
+        if kw["precision"] == 64:
+            assert rel_err(got[r], f_o) < 1e-9, r
+        else:
+            n = (kw["ny"], kw["nx"])
+            bound = fp32_force_bound(n, nsteps, fields[0], fields[3])
+            err = (np.abs(got[r] - f_o) / np.abs(f_o)).max()
+            print("batch run %d fp32 vs oracle: %.2e (bound %.2e)" % (r, err, bound))
+            assert err < bound, r

@@ -7,8 +7,8 @@ import functools
 import numpy as np
 import pytest
 
-from gpu_common import (A49, B21, TC49, RHOC49, droplet_ragged, gpu_run, lib, oracle_params, oracle_run,
-                        rel_err, slab64)
+from gpu_common import (A49, B21, TC49, RHOC49, droplet_ragged, fp32_force_bound, gpu_run, lib, oracle_params,
+                        oracle_run, rel_err, slab64)
 from oracle import fftlb_oracle as O
 from paper_1011_3582_gb300 import workloads as W
 
@@ -203,30 +203,6 @@ def _spinodal_oracle(n, nsteps):
     p = oracle_params(kw, integrator=3)
     f = O.run(O.init_equilibrium(*fields, p), p, nsteps)
     return fields, kw, f
-
-
-def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u_split=0.0):
-    """Elementwise bound on |df_i| / f_i of the FP32 path after nsteps RK3
-    steps.  Two sources: (1) each stage update rounds f_i at most twice, and
-    the initial f^eq once: 4 (S + 1) u with a factor 2 of margin; (2) the
-    force coefficient B (Eq. 21) contains d_b Lambda_ab with Lambda
-    containing K rho lap(rho) (Eq. 19), a third spectral derivative of rho.
-    The rounding of an FP32 transform is spread over all wavenumbers with rms
-    ~ u sqrt(log2 N) rms(rho) (two chained transforms: factor 2), and the
-    third derivative multiplies wavenumber k by |k|^3; over the square
-    spectrum of the window-4 symbol (max k_max = (2/dx)(1 + 1/6 + 3/40 +
-    5/112)) the rms of |k|^3 is 0.83 k_max^3.  |v - u| |dB| dt per stage,
-    over S = 3 nsteps stages, times sqrt(2 ln M) for the maximum over the M
-    values of f, times 2 of margin.  u_split: the relative error of one
-    split-BF16 first pass (the row and the column first passes of a 2-D
-    transform add 2 u_split to its u sqrt(log2 N))."""
-    u, N, S = 2.0 ** -24, n * n, 3 * nsteps
-    kmax = (2 / dx) * (1 + 1 / 6 + 3 / 40 + 5 / 112)
-    eps = (u * np.sqrt(np.log2(N)) + 2 * u_split) * np.sqrt(np.mean(rho ** 2))
-    d3 = 2 * eps * 0.83 * kmax ** 3
-    dB = vmax * K * d3 / T.min()
-    tail = np.sqrt(2 * np.log(33 * N))
-    return 4 * (S + 1) * u + 2 * tail * S * dt * dB
 
 
 @pytest.mark.parametrize("n,nsteps", [(256, 3), (384, 3), (512, 1)])

@@ -66,3 +66,27 @@ def test_gradient_of_sine_is_exact_k4(fl):
     out = grad_gpu(fl, g, 4, 64, dx=dx)
     assert np.abs(out[0] - np.cos(x)[None, :]).max() < 1e-13
     assert np.abs(out[1]).max() < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (1024, 1024), (512, 128)])
+def test_gradient_split_bf16_within_split_bound(fl, shape):
+    """Precision 32 | FFTLB_BF16SPLIT: the handle's gradient runs the
+    stage's transform code, whose first radix-16 pass of every row and
+    column transform is the split-BF16 DFT product on the tensor cores.
+    Bound: split_emulation.SPLIT_GRADIENT_BOUND (1.4e-4 of max |D g|),
+    derived from the split's rounding; a split pass without the w_hi x_lo
+    product gives about 3.6e-3 (tests/test_split_bound.py).  The plain fp32
+    path on the same input must stay below its own 2e-5, and the split
+    path must differ from it (the tensor-core pass ran)."""
+    from split_emulation import SPLIT_GRADIENT_BOUND
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal((1,) + shape)
+    split = grad_gpu(fl, g, 4, 32 | fl.BF16SPLIT)
+    plain = grad_gpu(fl, g, 4, 32)
+    for i, axis in enumerate(("x", "y")):
+        ref = O.D(g[0], axis, 1 / 256, 4)
+        es, e32 = rel_err(split[i], ref), rel_err(plain[i], ref)
+        print("split-BF16 gradient %s %s: %.2e (fp32 %.2e, bound %.2e)" % (shape, axis, es, e32, SPLIT_GRADIENT_BOUND))
+        assert es < SPLIT_GRADIENT_BOUND
+        assert e32 < 2e-5
+        assert not np.array_equal(split[i], plain[i])

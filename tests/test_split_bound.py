@@ -105,3 +105,39 @@ def test_dropping_a_term_breaks_the_bound():
     ye = exact(x, -1)
     err = np.abs(Y[:16] - ye.real) / mag[:16]
     assert err.max() > 10 * U_SPLIT
+
+
+def test_gradient_emulation_separates_complete_from_broken_split():
+    """The bound of the GPU split-BF16 gradient test (split_emulation): the
+    emulated gradient with complete split passes stays 4x below it, and with
+    the w_hi x_lo product dropped in every split pass it lands 4x above."""
+    from oracle import fftlb_oracle as O
+    from split_emulation import SPLIT_GRADIENT_BOUND, emulated_gradient
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal((256, 256))
+    for axis in ("x", "y"):
+        ref = O.D(g, axis, 1 / 256, 4)
+        scale = np.abs(ref).max()
+        ok = np.abs(emulated_gradient(g, axis, 1 / 256, 4) - ref).max() / scale
+        bad = np.abs(emulated_gradient(g, axis, 1 / 256, 4, drop_hi_lo=True) - ref).max() / scale
+        assert ok < SPLIT_GRADIENT_BOUND / 4, (axis, ok)
+        assert bad > 4 * SPLIT_GRADIENT_BOUND, (axis, bad)
+
+
+def test_gradient_emulation_without_splitting_is_exact():
+    """With exact products (no rounding at all) the emulated route equals
+    the oracle's D to round-off: the route itself is right."""
+    import split_emulation as S
+    from oracle import fftlb_oracle as O
+    rng = np.random.default_rng(1)
+    g = rng.standard_normal((64, 128))
+    saved = S._split, S.OPERAND
+    try:
+        S._split = lambda z: (np.asarray(z, np.float64), np.zeros(np.shape(z)))
+        S.OPERAND = np.float64
+        for axis in ("x", "y"):
+            ref = O.D(g, axis, 1 / 256, 3)
+            got = S.emulated_gradient(g, axis, 1 / 256, 3)
+            assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12
+    finally:
+        S._split, S.OPERAND = saved

@@ -39,7 +39,10 @@ def static_gradient(fl, g, window, dx):
 def test_static_gradient_matches_handle_gradient_on_consecutive_calls():
     fl = lib()
     rng = np.random.default_rng(2024)
-    cases = [((64, 64), 4, 1 / 256), ((48, 96), 2, 1 / 128), ((256, 256), 0, 1 / 256), ((64, 64), 4, 1 / 256)]
+    # (ny, nx): the limits of the array (nx or ny = 1024 at nx ny = 65536,
+    # 4-point axes) between ordinary grids, on consecutive calls
+    cases = [((64, 64), 4, 1 / 256), ((48, 96), 2, 1 / 128), ((256, 256), 0, 1 / 256), ((64, 1024), 4, 1 / 256),
+             ((1024, 64), 3, 1 / 256), ((4, 256), 4, 1 / 64), ((256, 4), 1, 1 / 64), ((64, 64), 4, 1 / 256)]
     for (ny, nx), window, dx in cases:
         g = rng.standard_normal((ny, nx))
         want = reference_gradient(fl, g, window, dx)
