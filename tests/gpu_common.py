@@ -64,7 +64,25 @@ def rel_err(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u_split=0.0):
+def weight_condition(T, speeds=(1.0, 1.9, 2.9, 4.3)):
+    """Largest condition number over the rings k of Eq. 4's weight
+    polynomial F_k(T) = T (c3 + T (c2 + T (c1 + T c0))) at the temperatures T:
+    sum_j |c_j T^j| / |F_k(T)|.  Near a root of F_k (ring 4 of the paper's
+    set near T = 0.43) fp32 evaluation loses that many ulps."""
+    T = np.asarray(T, np.float64)
+    worst = 0.0
+    for k in range(4):
+        o = [speeds[(k + l) % 4] ** 2 for l in (1, 2, 3)]
+        vk2 = speeds[k] ** 2
+        den = vk2 * (vk2 - o[0]) * (vk2 - o[1]) * (vk2 - o[2])
+        c = [48 / den, -6 * sum(o) / den, (o[0] * o[1] + o[1] * o[2] + o[2] * o[0]) / den,
+             -o[0] * o[1] * o[2] / (4 * den)]
+        terms = [c[0] * T ** 4, c[1] * T ** 3, c[2] * T ** 2, c[3] * T]
+        worst = max(worst, float((sum(np.abs(t) for t in terms) / np.abs(sum(terms))).max()))
+    return worst
+
+
+def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u_split=0.0, tau=1e-2):
     """Elementwise bound on |df_i| / f_i of the FP32 path after nsteps RK3
     steps.  Two sources: (1) each stage update rounds f_i at most twice, and
     the initial f^eq once: 4 (S + 1) u with a factor 2 of margin; (2) the
@@ -76,9 +94,14 @@ def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u
     spectrum of the window-4 symbol (max k_max = (2/dx)(1 + 1/6 + 3/40 +
     5/112)) the rms of |k|^3 is 0.83 k_max^3.  |v - u| |dB| dt per stage,
     over S = 3 nsteps stages, times sqrt(2 ln M) for the maximum over the M
-    values of f, times 2 of margin.  u_split: the relative error of one
-    split-BF16 first pass (the row and the column first passes of a 2-D
-    transform add 2 u_split to its u sqrt(log2 N))."""
+    values of f, times 2 of margin; (3) f^eq carries the fp32 error of the
+    weights F_k (Eq. 4), 4 u times the polynomial's condition number
+    (weight_condition), which the BGK term passes to f at dt / tau per
+    stage: S dt / tau 4 u cond, times 2 of margin (near a root of F_k, e.g.
+    ring 4 at T = 0.75 T_c of the 9/49, 2/21 fluid, this term dominates).
+    u_split: the relative error of one split-BF16 first pass (the row and
+    the column first passes of a 2-D transform add 2 u_split to its
+    u sqrt(log2 N))."""
     u, S = 2.0 ** -24, 3 * nsteps
     N = n * n if np.isscalar(n) else n[0] * n[1]   # n or (ny, nx)
     kmax = (2 / dx) * (1 + 1 / 6 + 3 / 40 + 5 / 112)
@@ -86,4 +109,5 @@ def fp32_force_bound(n, nsteps, rho, T, dx=1 / 256, dt=1e-5, K=1e-5, vmax=4.3, u
     d3 = 2 * eps * 0.83 * kmax ** 3
     dB = vmax * K * d3 / T.min()
     tail = np.sqrt(2 * np.log(33 * N))
-    return 4 * (S + 1) * u + 2 * tail * S * dt * dB
+    weights = 2 * S * (dt / tau) * 4 * u * weight_condition(T)
+    return 4 * (S + 1) * u + 2 * tail * S * dt * dB + weights
