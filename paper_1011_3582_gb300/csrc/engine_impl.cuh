@@ -437,6 +437,7 @@ static __global__ void k_reduce_partials(const double *partial, int ny, double *
 }  // namespace fftlb
 
 #include "kernels_pipe.cuh"
+#include "kernels_wr.cuh"
 
 namespace fftlb {
 
@@ -692,6 +693,13 @@ class EngineT : public Engine {
     std::vector<void *> allocs_;
     // group ranges in groups_
     int conv_groups_ = 0, l1_groups_ = 0, l2_groups_ = 0, grad_groups_ = 0, inv_groups_ = 0;
+    // warp-resident fp32 row kernels (kernels_wr.cuh) for nx = 512, 1024:
+    // their stage-1 twiddle table and launch shape
+    static constexpr bool wr_ok_ = std::is_same<real, float>::value && !SPLIT;
+    bool k5wr_ = false;
+    C *Tw1_ = nullptr;
+    size_t smem5w_ = 0;
+    int grid5w_ = 1;
     // gradient kernels (k_grad_*): column tile width and shared memory
     int TWg_ = 0;
     size_t smem_gr_ = 0, smem_gc_ = 0;
@@ -987,6 +995,20 @@ class EngineT : public Engine {
         if (ntr_) FFTLB_CU(cudaMemcpy(Tr_, tr.data(), tr.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntr8_) FFTLB_CU(cudaMemcpy(Tr8_, tr8.data(), tr8.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntc_) FFTLB_CU(cudaMemcpy(Tc_, tc.data(), tc.size() * sizeof(C), cudaMemcpyHostToDevice));
+        if (wr_ok_ && (h_ == 512 || h_ == 256)) {
+            // tw[k1 P + l] = exp(-2 pi i l k1 / h) for the row configuration of h
+            const int P = h_ == 512 ? 32 : 16, E = h_ / P;
+            std::vector<C> t1((size_t)h_);
+            const long double pi = 3.141592653589793238462643383279502884L;
+            for (int k1 = 0; k1 < E; ++k1)
+                for (int l = 0; l < P; ++l) {
+                    const long double a = 2.0L * pi * (long double)(l * k1) / (long double)h_;
+                    t1[(size_t)k1 * P + l].x = (real)cosl(a);
+                    t1[(size_t)k1 * P + l].y = (real)(-sinl(a));
+                }
+            if (!(st = dalloc(&Tw1_, t1.size())).good()) return st;
+            FFTLB_CU(cudaMemcpy(Tw1_, t1.data(), t1.size() * sizeof(C), cudaMemcpyHostToDevice));
+        }
         if (split_) {
             std::vector<uint4> fr;
             dft16_fragments(fr);
@@ -1414,6 +1436,25 @@ class EngineT : public Engine {
         st = occ_k5(smem5_, &nb);
         if (!st.good()) return st;
         grid5_ = std::min(B_ * ny_, std::max(1, nb) * nsm_);
+        return configure_wr();
+    }
+
+    // the warp-resident final row kernel where it applies (fp32, nx = 512 or
+    // 1024, and its shared memory fits)
+    Status configure_wr() {
+        if constexpr (wr_ok_) {
+            if ((h_ == 512 || h_ == 256) && Tw1_ && k5_wr_smem(h_) <= budget_) {
+                smem5w_ = k5_wr_smem(h_);
+                int nb = 0;
+                Status st = h_ == 512 ? occupancy(k5_wr<512>, NT5W, smem5w_, &nb)
+                                      : occupancy(k5_wr<256>, NT5W, smem5w_, &nb);
+                if (!st.good()) return st;
+                if (nb >= 1) {
+                    k5wr_ = true;
+                    grid5w_ = std::min(B_ * ny_, nb * nsm_);
+                }
+            }
+        }
         return Status::ok();
     }
 
@@ -1647,6 +1688,18 @@ class EngineT : public Engine {
         if (!(st = launch_col(l2_groups_, 3, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
+        if constexpr (wr_ok_) {
+            if (k5wr_) {
+                if (h_ == 512)
+                    k5_wr<512><<<grid5w_, NT5W, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
+                                                                    beta, Tw1_, Wp_, kp_, err_);
+                else
+                    k5_wr<256><<<grid5w_, NT5W, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
+                                                                    beta, Tw1_, Wp_, kp_, err_);
+                FFTLB_LAUNCHED("k5_wr");
+                return prof_end();
+            }
+        }
         const int ml5 = row_maxlr(CH5_, NT5);
         if (SMAX5_ == 1)
             k5_pipe<real, 1, SPLIT><<<grid5_, NT5, smem5_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha, beta, Wr_,

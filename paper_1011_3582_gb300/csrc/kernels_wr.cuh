@@ -1,0 +1,454 @@
+// Warp-resident row transforms and the fp32 row kernels built on them
+// (arXiv:1011.3582, Sec. 3.6, Fig. 3: transform, multiply, inverse).
+//
+// A row of H = E * P complex values (a real row of 2H values packed as
+// z[m] = x[2m] + i x[2m+1]) is transformed by a group of P lanes of one
+// warp, in place in shared memory, with no block barrier:
+//   stage 1: lane l holds x[l + P t] (t < E) in registers and takes the
+//            E-point DFT over t, then multiplies output k1 by W_H^(l k1);
+//   transpose: every lane stores its E values at swizzled positions of the
+//            same row buffer (__syncwarp before and after);
+//   stage 2: the P-point DFTs over l, one per k1, in registers: for P <= E
+//            lane j holds the P values of k1 = j + P q (q < E / P); for
+//            P = 2E (H = 512) lane k1 + E g holds the even (g = 0) or odd
+//            (g = 1) half of the l values, takes an E-point DFT and the
+//            last radix-2 step is one exchange with lane ^ E (__shfl_xor);
+//   result:  X[k1 + E k2] back in natural order.
+// With n = l + P t and k = k1 + E k2, W_H^(nk) = W_H^(l k1) W_P^(l k2)
+// W_E^(t k1), which is the decomposition above.  Every index is a
+// compile-time constant plus the lane's own offset, and the swizzles keep
+// the shared-memory accesses free of bank conflicts for the P >= 16
+// layouts (the row groups of P = 8 share banks two ways).
+#pragma once
+
+#include "kernels_pipe.cuh"
+
+namespace fftlb {
+
+// cos(2 pi k / 32), k = 0..8 (the rest by symmetry)
+__device__ __forceinline__ constexpr double cos32(int k) {
+    return k == 0 ? 1.0
+         : k == 1 ? 0.98078528040323044913
+         : k == 2 ? 0.92387953251128675613
+         : k == 3 ? 0.83146961230254523708
+         : k == 4 ? 0.70710678118654752440
+         : k == 5 ? 0.55557023301960222474
+         : k == 6 ? 0.38268343236508977173
+         : k == 7 ? 0.19509032201612826785
+                  : 0.0;
+}
+
+// W_32^k = exp(DIR 2 pi i k / 32) for 0 <= k < 16, compile-time after unrolling
+template <int DIR, typename R>
+__device__ __forceinline__ void w32(int k, R &c, R &s) {
+    const double cc = k <= 8 ? cos32(k) : -cos32(16 - k);
+    const double ss = k <= 8 ? cos32(8 - k) : cos32(k - 8);
+    c = R(cc);
+    s = R(DIR < 0 ? -ss : ss);
+}
+
+// 32-point DFT as two 16-point DFTs of the even and odd inputs and one
+// radix-2 step with the constants W_32^k
+template <int DIR, typename C> struct SmallDFT<32, DIR, C> {
+    __device__ __forceinline__ static void run(C *v) {
+        using R = decltype(v[0].x);
+        C e[16], o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        SmallDFT<16, DIR, C>::run(e);
+        SmallDFT<16, DIR, C>::run(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            R c, s;
+            w32<DIR, R>(k, c, s);
+            const C t = k == 0 ? o[k] : C{o[k].x * c - o[k].y * s, o[k].x * s + o[k].y * c};
+            v[k] = cadd(e[k], t);
+            v[k + 16] = csub(e[k], t);
+        }
+    }
+};
+
+// Row configurations: H = E * P, P lanes per row, 32 / P rows per warp
+template <int H> struct RowCfg;
+template <> struct RowCfg<512> { static constexpr int E = 16, P = 32; };
+template <> struct RowCfg<256> { static constexpr int E = 16, P = 16; };
+template <> struct RowCfg<128> { static constexpr int E = 16, P = 8; };
+
+// position of stage-1 output (l, k1) in the row buffer.  P >= 16: k1 P +
+// (l ^ (k1 mod P)) (for P = 2E, k1 < E: k1 P + (l ^ k1)); P = 8: the row
+// parity rsw also flips bit 0 of k1, so that the two rows of a half-warp use
+// different banks
+template <int H>
+__device__ __forceinline__ int tpos(int l, int k1, int rsw) {
+    constexpr int P = RowCfg<H>::P;
+    return ((k1 ^ rsw) * P) + (l ^ (k1 & (P - 1)));
+}
+
+// the lanes of this lane's row group (P consecutive lanes)
+template <int P>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (P >= 32) return 0xffffffffu;
+    else return ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
+}
+
+// In-place DFT (DIR = -1) or unnormalised inverse (DIR = +1) of the H
+// complex values at z by lane j (0 <= j < P) of its row group; tw[k1 P + l]
+// = exp(-2 pi i l k1 / H); rsw: row parity (P = 8), else 0.  All P lanes of
+// the row group must call it together (they synchronise with __syncwarp on
+// the group's mask; other row groups of the warp may diverge).
+template <int H, int DIR, typename C>
+__device__ __forceinline__ void row_fft_wr(C *z, const C *tw, int j, int rsw) {
+    constexpr int E = RowCfg<H>::E, P = RowCfg<H>::P;
+    const unsigned gm = group_mask<P>();
+    C v[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) v[t] = z[j + P * t];
+    SmallDFT<E, DIR, C>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < E; ++k1) {
+        C w = tw[k1 * P + j];
+        if (DIR > 0) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+    __syncwarp(gm);
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) z[tpos<H>(j, k1, rsw)] = v[k1];
+    __syncwarp(gm);
+    if constexpr (P <= E) {
+        constexpr int NQ = E / P;
+        C u[NQ][P];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+            for (int l = 0; l < P; ++l) u[q][l] = z[tpos<H>(l, j + P * q, rsw)];
+            SmallDFT<P, DIR, C>::run(u[q]);
+        }
+        __syncwarp(gm);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) z[j + P * q + E * k2] = u[q][k2];
+    } else {
+        static_assert(P == 2 * E, "row configuration");
+        using R = decltype(v[0].x);
+        constexpr int HE = E / 2;
+        const int k1 = j & (E - 1), g = j / E;
+        C u[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) u[m] = z[tpos<H>(g + 2 * m, k1, 0)];
+        SmallDFT<E, DIR, C>::run(u);
+        // X[k1 + E (k2' + E k3)] = V0[k2'] + (-1)^k3 W_P^k2' V1[k2']: lane
+        // g keeps k2' in [HE g, HE g + HE) and receives the other lane's half
+        C a[HE], b[HE];
+#pragma unroll
+        for (int i = 0; i < HE; ++i) {
+            const C send = g ? u[i] : u[HE + i];
+            C recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, send.x, E);
+            recv.y = __shfl_xor_sync(0xffffffffu, send.y, E);
+            a[i] = g ? recv : u[i];
+            b[i] = g ? u[HE + i] : recv;
+        }
+        __syncwarp(gm);   // every lane's stage-2 reads are done
+#pragma unroll
+        for (int i = 0; i < HE; ++i) {
+            R c, s;
+            w32<DIR, R>(i, c, s);   // W_P^i, P = 32
+            C t = i == 0 ? b[i] : C{b[i].x * c - b[i].y * s, b[i].x * s + b[i].y * c};
+            // times W_P^(HE g): W_32^8 = -i forward, +i inverse
+            const C r = DIR < 0 ? cmul_mi(t) : cmul_i(t);
+            t = g ? r : t;
+            const int k2 = HE * g + i;
+            z[k1 + E * k2] = cadd(a[i], t);
+            z[k1 + E * (k2 + E)] = csub(a[i], t);
+        }
+        __syncwarp(gm);
+        return;
+    }
+    __syncwarp(gm);
+}
+
+// Forward real rows: the natural-order result Z of row_fft_wr (the
+// half-length transform of the packed row) -> one-sided spectrum X[0 .. H-1]
+// with the real Nyquist value in the imaginary part of X[0], written to
+// out (global memory, coalesced: lanes take consecutive k and H - k).
+// Wp[k] = exp(-2 pi i k / 2H), k <= H / 2.
+template <int H, typename C>
+__device__ __forceinline__ void r2c_post_wr(const C *z, C *out, const C *Wp, int j) {
+    using R = decltype(z[0].x);
+    constexpr int P = RowCfg<H>::P;
+#pragma unroll
+    for (int k0 = 0; k0 <= H / 2; k0 += P) {
+        const int k = k0 + j;
+        if (k > H / 2) break;
+        if (k == 0) {
+            const C z0 = z[0];
+            out[0] = C{z0.x + z0.y, z0.x - z0.y};
+        } else {
+            const C p = z[k], q = z[H - k];
+            const C ze = cscale(cadd(p, cconj(q)), R(0.5));
+            const C zo = cscale(cmul_mi(csub(p, cconj(q))), R(0.5));
+            const C wz = cmul(Wp[k], zo);
+            out[k] = cadd(ze, wz);
+            if (H - k != k) out[H - k] = cconj(csub(ze, wz));
+        }
+    }
+}
+
+// Inverse real rows, in place: one-sided packed spectrum X -> Z[k] = (X[k]
+// + X[k + H]) + i (X[k] - X[k + H]) exp(+2 pi i k / 2H), X[k + H] =
+// conj X[H - k]; the half-length inverse of Z is the real row.
+template <int H, typename C>
+__device__ __forceinline__ void c2r_pre_wr(C *z, const C *Wp, int j) {
+    constexpr int P = RowCfg<H>::P;
+#pragma unroll
+    for (int k0 = 0; k0 <= H / 2; k0 += P) {
+        const int k = k0 + j;
+        if (k > H / 2) break;
+        if (k == 0) {
+            const C x0 = z[0];
+            z[0] = C{x0.x + x0.y, x0.x - x0.y};
+        } else {
+            const C p = z[k], q = z[H - k];
+            const C w = Wp[k];
+            const C wc = cconj(w);
+            z[k] = cadd(cadd(p, cconj(q)), cmul_i(cmul(csub(p, cconj(q)), wc)));
+            if (H - k != k) {
+                const C mw = C{-w.x, -w.y};
+                z[H - k] = cadd(cadd(q, cconj(p)), cmul_i(cmul(csub(q, cconj(p)), mw)));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5 (fp32, nx = 2H): convection rows + level-2 divergences (inverse) ->
+// A, B, C, C_q (Eqs. 20-23), f^eq (Eq. 3), I (Eq. 11), BGK and the RK
+// combination (Eq. 10), as k5_pipe, with warp-resident row transforms.
+// Persistent over the rows of all runs; per row: the head (3 level-2
+// spectra, rho, u_x, u_y, T, the 3 aux numerators; two buffers, prefetched
+// a row ahead) and 32 / CH chunks of CH convection rows (two buffers), each
+// chunk one row per row group (CH = 16 warps x rows per warp: two rings for
+// H = 512, all four for H = 256).
+// ---------------------------------------------------------------------------
+
+constexpr int NT5W = 512;
+
+template <int H>
+__global__ void __launch_bounds__(NT5W, 1) k5_wr(const float2 *spec, const float *__restrict__ fields,
+                                                 const float *__restrict__ aux, const float *fcur, const float *fbase,
+                                                 float *fout, float alpha, float beta,
+                                                 const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
+                                                 KP<float> P, int *err) {
+    using C = float2;
+    using real = float;
+    constexpr int NX = 2 * H, NT = NT5W, NWARP = NT / 32;
+    constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;          // lanes per row, rows per warp
+    constexpr int CH = NWARP * RPW, NCH = NMOV / CH;           // rows per chunk, chunks per row
+    constexpr int NRING = CH / 8;                              // rings per chunk
+    constexpr int SMAX = (NX + NT - 1) / NT;
+    static_assert(NMOV % CH == 0 && CH % 8 == 0, "chunking");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1, hbar0, hbar1;
+    const int nx = NX, ny = P.ny, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grow = warp * RPW + lane / PL, j = lane & (PL - 1);   // row within the chunk, lane within the row
+    const int rsw = PL == 8 ? ((lane / PL) & 1) : 0;
+    const size_t N = (size_t)NX * ny, slot = (size_t)ny * H;
+    SmemCursor sc{smem_raw, 0u};
+    C *tw = (C *)sc.take(H * sizeof(C));
+    C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
+    real *head0 = (real *)sc.take((size_t)NHEAD * NX * sizeof(real));
+    real *head1 = (real *)sc.take((size_t)NHEAD * NX * sizeof(real));
+    real *buf0 = (real *)sc.take((size_t)CH * NX * sizeof(real));
+    real *buf1 = (real *)sc.take((size_t)CH * NX * sizeof(real));
+    const int NY = P.nrun * ny;
+    const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs = nrows * NCH;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init(&hbar0, 1);
+        mbar_init(&hbar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(tw, tw_g, H, NT);
+    load_tab(Wp, Wp_g, H / 2 + 1, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, H);
+        if (nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, H);
+        if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, NCH, CH, nx, ny, slot, H);
+        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, NCH, CH, nx, ny, slot, H);
+    }
+    uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
+    bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = nrows > 1;
+    const real dt = P.dt, itau = real(1) / P.tau;
+    const bool with_base = alpha != real(0);
+    for (int jb = 0; jb < njobs; ++jb) {
+        const bool odd = jb & 1;
+        const int ri = jb / NCH, c = jb - ri * NCH;
+        const bool hodd = ri & 1;
+        const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int run = yg / ny, y = yg - run * ny;
+        const size_t fo = (size_t)run * Q * N;
+        real *Hd = hodd ? head1 : head0;
+        if (c == 0) {
+            if (!block_wait(hodd ? &hbar1 : &hbar0, hodd ? hpar1 : hpar0, err)) {
+                if (pend0) mbar_wait_bounded(&bar0, par0);
+                if (pend1) mbar_wait_bounded(&bar1, par1);
+                if (hpend0) mbar_wait_bounded(&hbar0, hpar0);
+                if (hpend1) mbar_wait_bounded(&hbar1, hpar1);
+                return;
+            }
+            if (hodd) {
+                hpar1 ^= 1;
+                hpend1 = false;
+            } else {
+                hpar0 ^= 1;
+                hpend0 = false;
+            }
+        }
+        if (!block_wait(odd ? &bar1 : &bar0, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            if (hpend0) mbar_wait_bounded(&hbar0, hpar0);
+            if (hpend1) mbar_wait_bounded(&hbar1, hpar1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        real *B = odd ? buf1 : buf0;
+        // inverse transforms: convection row grow of the chunk; with the
+        // first chunk, the 3 level-2 rows of the head (row groups 0..2)
+        {
+            const unsigned gm = group_mask<PL>();
+            C *zr = reinterpret_cast<C *>(B) + (size_t)grow * H;
+            c2r_pre_wr<H>(zr, Wp, j);
+            __syncwarp(gm);
+            row_fft_wr<H, +1>(zr, tw, j, rsw);
+            if (c == 0 && grow < 3) {   // uniform over each row group
+                C *zh = reinterpret_cast<C *>(Hd) + (size_t)grow * H;
+                c2r_pre_wr<H>(zh, Wp, j);
+                __syncwarp(gm);
+                row_fft_wr<H, +1>(zh, tw, j, rsw);
+            }
+        }
+        __syncthreads();
+        if (c == 0) {
+            // per-site coefficients over the head rows (same site, same
+            // thread): row 0 <- e0, 1 <- e1x, 2 <- e1y, 7 <- C + C_q, 8 <- 1/T;
+            // the rest velocity's update
+#pragma unroll 1
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x < nx) {
+                    const real rho = Hd[3 * nx + x], ux = Hd[4 * nx + x], uy = Hd[5 * nx + x], T = Hd[6 * nx + x];
+                    const real dLx = Hd[x], dLy = Hd[nx + x], dPh = Hd[2 * nx + x];
+                    const real rT = rho * T;
+                    const real inv2 = real(1) / (real(2) * rho * T * T);
+                    const real Bx = (Hd[8 * nx + x] + dLx) / rT;      // Eq. 21
+                    const real By = (Hd[9 * nx + x] + dLy) / rT;
+                    const real CC = (Hd[7 * nx + x] + dPh) * inv2;    // C + C_q, Eqs. 22-23
+                    const real A = real(-2) * CC * T;                 // Eq. 20
+                    const real u2 = ux * ux + uy * uy;
+                    const real e0 = A - (Bx * ux + By * uy) + CC * u2;
+                    Hd[x] = e0;
+                    Hd[nx + x] = Bx - real(2) * CC * ux;
+                    Hd[2 * nx + x] = By - real(2) * CC * uy;
+                    Hd[7 * nx + x] = CC;
+                    Hd[8 * nx + x] = real(1) / T;
+                    real F[5];
+                    weights_Fk<real>(T, F);
+                    const real qq = real(0.5) * u2 / T, om = real(1) - qq;
+                    const real fe = rho * F[0] * (om + real(0.5) * qq * qq);
+                    const size_t o = fo + (size_t)y * nx + x;
+                    const real fc = fcur[o];
+                    real fn = beta * (fc + dt * (-(fc - fe) * itau - e0 * fe));
+                    if (with_base) fn += alpha * fbase[o];
+                    fout[o] = fn;
+                }
+            }
+            __syncthreads();
+        }
+        // epilogue: the NRING rings of the chunk (ring k = c NRING + rr:
+        // velocities 1 + 8k .. 8 + 8k of Eq. 1, one speed, one weight, the
+        // eight directions known at compile time)
+#pragma unroll 1
+        for (int rr = 0; rr < NRING; ++rr) {
+            const int k = c * NRING + rr;
+            const int v0 = 8 * k;
+            const real sk = VX<real>(1 + v0), sk2 = V2<real>(1 + v0);
+            const real *cres = B + (size_t)rr * 8 * NX;
+#pragma unroll 1
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                if (x >= nx) continue;
+                real fc[8], fb[8];
+                const size_t o0 = fo + (size_t)(1 + v0) * N + (size_t)y * nx + x;
+                const real *pc = fcur + o0;
+                const real *pb = fbase + o0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    fc[r] = pc[r * N];
+                    fb[r] = with_base ? pb[r * N] : real(0);
+                }
+                real *po = fout + o0;
+                const real rho = Hd[3 * nx + x], ux = Hd[4 * nx + x], uy = Hd[5 * nx + x], T = Hd[6 * nx + x];
+                const real iT = Hd[8 * nx + x];
+                const real e0 = Hd[x], e1x = Hd[nx + x], e1y = Hd[2 * nx + x], CC = Hd[7 * nx + x];
+                const real Fk = T * (FKC<real>(k, 3) + T * (FKC<real>(k, 2) + T * (FKC<real>(k, 1) + T * FKC<real>(k, 0))));   // Eq. 4
+                const real qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
+                const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
+                const real p3 = iT * iT * iT * (real(1) / real(6)), p4 = iT * iT * iT * iT * (real(1) / real(24));
+                const real rF = rho * Fk;
+                const real g0 = e0 + CC * sk2;
+                const real uxk = sk * ux, uyk = sk * uy, exk = sk * e1x, eyk = sk * e1y;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const real vu = dir_dot<real>(r, uxk, uyk);
+                    const real br = p0 + vu * (p1 + vu * (p2 + vu * (p3 + vu * p4)));
+                    const real fe = rF * br;                                                 // Eq. 3
+                    const real I = -(g0 + dir_dot<real>(r, exk, eyk)) * fe;                   // Eq. 11
+                    const real conv = cres[(size_t)r * NX + x];
+                    const real rhs = -conv - (fc[r] - fe) * itau + I;                        // Eq. 10
+                    real fn = beta * (fc[r] + dt * rhs);
+                    if (with_base) fn += alpha * fb[r];
+                    po[r * N] = fn;
+                }
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            if (jb + 2 < njobs) {
+                const bool nodd = jb & 1;   // chunk jb + 2 reuses this buffer
+                k5_issue_chunk<real>(spec, B, nodd ? &bar1 : &bar0, jb + 2, NCH, CH, nx, ny, slot, H);
+                if (nodd) pend1 = true;
+                else pend0 = true;
+            }
+            if (c == NCH - 1 && ri + 2 < nrows) {
+                k5_issue_head<real>(spec, fields, aux, Hd, hodd ? &hbar1 : &hbar0, ri + 2, nx, ny, N, slot, H);
+                if (hodd) hpend1 = true;
+                else hpend0 = true;
+            }
+        }
+    }
+}
+
+// shared memory of k5_wr<H>
+inline size_t k5_wr_smem(int H) {
+    const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
+    const int CH = (NT5W / 32) * (32 / P);
+    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)NHEAD * 2 * H * 4, (size_t)NHEAD * 2 * H * 4,
+                       (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4});
+}
+
+}  // namespace fftlb

@@ -30,6 +30,11 @@ def spinodal_case(n, Tr, precision, seed):
     return fields, dict(nx=n, ny=n, a=A49, b=B21, precision=precision, integrator=3)
 
 
+def wide_case(nx, ny, Tr, seed):
+    fields = W.spinodal(nx, ny, 1 / (3 * B21), Tr * TC49, amp=0.01, seed=seed)
+    return fields, dict(nx=nx, ny=ny, a=A49, b=B21, precision=32, integrator=3)
+
+
 def test_batch_matches_single_handles(fl):
     cases = [slab_case(64, 0.9, 64, 1), slab_case(48, 0.8, 64, 2), slab_case(128, 0.95, 32, 3),
              slab_case(96, 0.75, 32, 4), spinodal_case(256, 0.8, 32, 5), spinodal_case(384, 0.9, 32, 6),
@@ -107,13 +112,15 @@ def test_batch_runs_match_oracle(fl):
     compared run by run with the FP64 oracle after 3 SSP-RK3 steps: two
     64^2 slabs at different temperatures share one group (one launch over
     both runs), a 48 x 96 droplet has radix-3 axes, and two 128^2 spinodal
-    quenches share an fp32 group beside a 96^2 fp32 slab.  FP64 runs: the
+    quenches share an fp32 group beside a 96^2 fp32 slab and two 32 x 512
+    quenches (the warp-resident row kernels over two runs).  FP64 runs: the
     1e-9 bar; FP32 runs: fp32_force_bound elementwise."""
     nsteps = 3
     drop_fields, drop_kw = droplet_ragged()
     cases = [slab_case(64, 0.9, 64, 21), slab_case(64, 0.8, 64, 22),
              (drop_fields, dict(drop_kw, precision=64, integrator=3)),
-             spinodal_case(128, 0.8, 32, 23), spinodal_case(128, 0.75, 32, 24), slab_case(96, 0.85, 32, 25)]
+             spinodal_case(128, 0.8, 32, 23), spinodal_case(128, 0.75, 32, 24), slab_case(96, 0.85, 32, 25),
+             wide_case(512, 32, 0.8, 26), wide_case(512, 32, 0.85, 27)]
     with fl.Batch([fl.params(**kw) for _, kw in cases], autotune=True) as b:
         for r, (fields, _) in enumerate(cases):
             b.set_fields(r, *fields)

@@ -378,3 +378,24 @@ def test_droplet_512_precision_config(fl, precision):
         name = "split-BF16" if split else "fp32"
         print(f"{name} 512^2 droplet after 1 RK3 step: max |df|/f = {err:.3e} (bound {bound:.3e})")
         assert err < bound
+
+
+@pytest.mark.parametrize("nx,ny", [(1024, 32), (512, 48), (512, 16), (1024, 96)])
+def test_wide_rows_fp32(fl, nx, ny):
+    """Row widths nx = 512 and 1024, where the fp32 path runs its
+    warp-resident row kernels, on narrow grids (columns of 16 to 96, the
+    radix-3 lengths 48 and 96 included) against the oracle after 3 SSP-RK3
+    steps of a spinodal quench at T = 0.8 T_c, element by element within
+    fp32_force_bound."""
+    kw = dict(nx=nx, ny=ny, a=A49, b=B21)
+    fields = W.spinodal(nx, ny, RHOC49, 0.8 * TC49, amp=0.01, seed=nx + ny)
+    p = oracle_params(kw, integrator=3)
+    f_o = O.run(O.init_equilibrium(*fields, p), p, 3)
+    with fl.Handle(fl.params(integrator=3, precision=32, **kw)) as h:
+        h.set_fields(*fields)
+        h.step(3)
+        f_g = h.get_f()
+    bound = fp32_force_bound((ny, nx), 3, fields[0], fields[3])
+    err = (np.abs(f_g - f_o) / np.abs(f_o)).max()
+    print("fp32 %dx%d vs oracle: %.2e (bound %.2e)" % (ny, nx, err, bound))
+    assert err < bound

@@ -1,0 +1,146 @@
+"""Host mirror of the warp-resident row transform of kernels_wr.cuh
+(row_fft_wr, r2c_post_wr, c2r_pre_wr): the same index arithmetic, with
+numpy arrays for a row group's shared-memory row and its lanes' registers,
+so that tests can check it against numpy's FFT and count shared-memory
+bank conflicts without a GPU.  Test infrastructure: no method arithmetic."""
+import numpy as np
+
+ROWCFG = {512: (16, 32), 256: (16, 16), 128: (16, 8)}   # H: (E, P)
+
+
+def tpos(H, l, k1, rsw):
+    E, P = ROWCFG[H]
+    return ((k1 ^ rsw) * P) + (l ^ (k1 & (P - 1)))
+
+
+def dft(v, direction):
+    n = len(v)
+    m = np.arange(n)
+    return np.exp(direction * 2j * np.pi * np.outer(m, m) / n) @ v
+
+
+class Recorder:
+    """Records every shared-memory access as (instruction id, lane, word)."""
+
+    def __init__(self):
+        self.acc = {}
+
+    def add(self, iid, lane, word):
+        self.acc.setdefault(iid, []).append((lane, word))
+
+    def worst_conflict(self, word_bytes=8):
+        """Largest number of distinct words one bank serves in one
+        half-warp (8-byte accesses) or warp (4-byte) of one instruction."""
+        worst = 1
+        for iid, lst in self.acc.items():
+            groups = {}
+            for lane, w in lst:
+                grp = lane // 16 if word_bytes == 8 else 0
+                groups.setdefault(grp, set()).add(w)
+            for ws in groups.values():
+                banks = {}
+                for w in ws:
+                    b = (w * word_bytes // 4) % 32
+                    banks.setdefault(b, set()).add(w)
+                worst = max(worst, max(len(s) for s in banks.values()))
+        return worst
+
+
+def row_fft_wr(z, H, direction, rsw=0, rec=None, row=0):
+    """Emulates row_fft_wr on the row z (complex array of length H) for one
+    row group; returns the transformed row (z is not modified)."""
+    E, P = ROWCFG[H]
+    z = z.astype(complex).copy()
+    tw = np.exp(-2j * np.pi * np.outer(np.arange(E), np.arange(P)) / H)   # tw[k1, l]
+    lane0 = (row % (32 // P)) * P if P < 32 else 0
+    regs = []
+    for j in range(P):
+        v = np.array([z[j + P * t] for t in range(E)])
+        if rec:
+            for t in range(E):
+                rec.add(("s1load", t), lane0 + j, row * H + j + P * t)
+        v = dft(v, direction)
+        w = tw[:, j] if direction < 0 else np.conj(tw[:, j])
+        regs.append(v * w)
+    for j in range(P):
+        for k1 in range(E):
+            z[tpos(H, j, k1, rsw)] = regs[j][k1]
+            if rec:
+                rec.add(("tstore", k1), lane0 + j, row * H + tpos(H, j, k1, rsw))
+    out = z.copy()
+    if P <= E:
+        for j in range(P):
+            for q in range(E // P):
+                k1 = j + P * q
+                u = np.array([z[tpos(H, l, k1, rsw)] for l in range(P)])
+                if rec:
+                    for l in range(P):
+                        rec.add(("s2load", q, l), lane0 + j, row * H + tpos(H, l, k1, rsw))
+                u = dft(u, direction)
+                for k2 in range(P):
+                    out[k1 + E * k2] = u[k2]
+                    if rec:
+                        rec.add(("nstore", q, k2), lane0 + j, row * H + k1 + E * k2)
+        return out
+    assert P == 2 * E
+    HE = E // 2
+    V = {}
+    for j in range(P):
+        k1, g = j & (E - 1), j // E
+        u = np.array([z[tpos(H, g + 2 * m, k1, 0)] for m in range(E)])
+        if rec:
+            for m in range(E):
+                rec.add(("s2load", m), j, tpos(H, g + 2 * m, k1, 0))
+        V[j] = dft(u, direction)
+    for j in range(P):
+        k1, g = j & (E - 1), j // E
+        partner = j ^ E
+        for i in range(HE):
+            send_p = V[partner][i] if (partner // E) else V[partner][HE + i]   # what the partner sends
+            a = send_p if g else V[j][i]
+            b = V[j][HE + i] if g else send_p
+            w = np.exp(direction * 2j * np.pi * i / 32)
+            t = b * w
+            if g:
+                t = t * (-1j if direction < 0 else 1j)
+            k2 = HE * g + i
+            out[k1 + E * k2] = a + t
+            out[k1 + E * (k2 + E)] = a - t
+            if rec:
+                rec.add(("nstore", i, 0), j, k1 + E * k2)
+                rec.add(("nstore", i, 1), j, k1 + E * (k2 + E))
+    return out
+
+
+def r2c_post(Z, H):
+    """Emulates r2c_post_wr: packed one-sided spectrum from the transform Z."""
+    out = np.zeros(H, complex)
+    Wp = np.exp(-2j * np.pi * np.arange(H // 2 + 1) / (2 * H))
+    for k in range(H // 2 + 1):
+        if k == 0:
+            out[0] = complex(Z[0].real + Z[0].imag, Z[0].real - Z[0].imag)
+            continue
+        p, q = Z[k], Z[H - k]
+        ze = 0.5 * (p + np.conj(q))
+        zo = -0.5j * (p - np.conj(q))
+        wz = Wp[k] * zo
+        out[k] = ze + wz
+        if H - k != k:
+            out[H - k] = np.conj(ze - wz)
+    return out
+
+
+def c2r_pre(X, H):
+    """Emulates c2r_pre_wr."""
+    z = X.astype(complex).copy()
+    Wp = np.exp(-2j * np.pi * np.arange(H // 2 + 1) / (2 * H))
+    for k in range(H // 2 + 1):
+        if k == 0:
+            z[0] = complex(X[0].real + X[0].imag, X[0].real - X[0].imag)
+            continue
+        p, q = X[k], X[H - k]
+        w = Wp[k]
+        z[k] = (p + np.conj(q)) + 1j * ((p - np.conj(q)) * np.conj(w))
+        if H - k != k:
+            z[H - k] = (q + np.conj(p)) + 1j * ((q - np.conj(p)) * (-w))
+    return z
