@@ -700,6 +700,12 @@ class EngineT : public Engine {
     C *Tw1_ = nullptr;
     size_t smem5w_ = 0;
     int grid5w_ = 1;
+    // warp-resident convection columns for ny = 256, 512, 1024
+    bool colwr_ = false;
+    C *Twc_ = nullptr;
+    size_t smemcw_ = 0;
+    int gridcw_ = 1, nbufcw_ = 1;
+    CUtensorMap tmap_convw_{};
     // gradient kernels (k_grad_*): column tile width and shared memory
     int TWg_ = 0;
     size_t smem_gr_ = 0, smem_gc_ = 0;
@@ -1008,6 +1014,20 @@ class EngineT : public Engine {
                 }
             if (!(st = dalloc(&Tw1_, t1.size())).good()) return st;
             FFTLB_CU(cudaMemcpy(Tw1_, t1.data(), t1.size() * sizeof(C), cudaMemcpyHostToDevice));
+        }
+        if (wr_ok_ && (ny_ == 1024 || ny_ == 512 || ny_ == 256)) {
+            // twc[k1 P + l] = exp(-2 pi i l k1 / ny) for the column configuration of ny
+            const int P = ny_ == 1024 ? 32 : 16, E = ny_ / P;
+            std::vector<C> t1((size_t)ny_);
+            const long double pi = 3.141592653589793238462643383279502884L;
+            for (int k1 = 0; k1 < E; ++k1)
+                for (int l = 0; l < P; ++l) {
+                    const long double a = 2.0L * pi * (long double)(l * k1) / (long double)ny_;
+                    t1[(size_t)k1 * P + l].x = (real)cosl(a);
+                    t1[(size_t)k1 * P + l].y = (real)(-sinl(a));
+                }
+            if (!(st = dalloc(&Twc_, t1.size())).good()) return st;
+            FFTLB_CU(cudaMemcpy(Twc_, t1.data(), t1.size() * sizeof(C), cudaMemcpyHostToDevice));
         }
         if (split_) {
             std::vector<uint4> fr;
@@ -1454,6 +1474,31 @@ class EngineT : public Engine {
                     grid5w_ = std::min(B_ * ny_, nb * nsm_);
                 }
             }
+            const int TWw = ny_ == 1024 ? 8 : 16, NTw = TWw * (ny_ == 1024 ? 32 : 16);
+            if (Twc_ && h_ % TWw == 0) {
+                // one or two tile buffers: the most blocks per SM, then two
+                int best = 0;
+                for (int nb2 = 2; nb2 >= 1; --nb2) {
+                    const size_t sm = kcol_wr_smem(ny_, h_, nb2);
+                    if (sm > budget_) continue;
+                    int nb = 0;
+                    Status st = ny_ == 1024 ? occupancy(kcol_wr<1024>, NTw, sm, &nb)
+                              : ny_ == 512  ? occupancy(kcol_wr<512>, NTw, sm, &nb)
+                                            : occupancy(kcol_wr<256>, NTw, sm, &nb);
+                    if (!st.good()) return st;
+                    if (nb > best) {
+                        best = nb;
+                        nbufcw_ = nb2;
+                        smemcw_ = sm;
+                    }
+                }
+                if (best > 0) {
+                    Status st = make_tmap(&tmap_convw_, TWw);
+                    if (!st.good()) return st;
+                    colwr_ = true;
+                    gridcw_ = best * nsm_;
+                }
+            }
         }
         return Status::ok();
     }
@@ -1640,6 +1685,21 @@ class EngineT : public Engine {
 
   private:
     Status launch_col(int first, int count, bool level1) {
+        if constexpr (wr_ok_) {
+            if (!level1 && colwr_) {
+                if (ny_ == 1024)
+                    kcol_wr<1024><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
+                                                                       kp_, BOXR_, nbufcw_, tmap_convw_, err_);
+                else if (ny_ == 512)
+                    kcol_wr<512><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
+                                                                      kp_, BOXR_, nbufcw_, tmap_convw_, err_);
+                else
+                    kcol_wr<256><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
+                                                                      kp_, BOXR_, nbufcw_, tmap_convw_, err_);
+                FFTLB_LAUNCHED("kcol_wr");
+                return Status::ok();
+            }
+        }
         if (level1)
             kcol_pipe<real, true, SPLIT><<<gridl_, NTC, smeml_, stream_>>>(specb_, groups_ + first, count, kxt_,
                                                                                kyt_, Wc_, Tc_, ntc_, kp_, TWl_, BOXR_,

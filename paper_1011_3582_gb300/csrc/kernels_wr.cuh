@@ -443,6 +443,167 @@ __global__ void __launch_bounds__(NT5W, 1) k5_wr(const float2 *spec, const float
     }
 }
 
+// ---------------------------------------------------------------------------
+// Column transforms of a tile of TW spectrum columns of length NY = E * P
+// (the tile [NY][TW] complex as the tensor copy lands it): thread (c, l)
+// (c < TW fastest, l < P) holds column c's x[l + P t], t < E:
+//   stage 1: E-point DFT over t, times W_NY^(l k1), stored in place at row
+//            k1 P + (l ^ (k1 & SW)) of the tile (SW = 16 / TW - 1: the row
+//            swizzle that keeps stage 2's reads conflict-free; the rows it
+//            exchanges belong to threads of the same warp, so __syncwarp
+//            orders the in-place store);
+//   __syncthreads;
+//   stage 2: thread (c, j) takes k1 = j + P q (q < E / P) and the P-point
+//            DFT over l: the spectrum X[k1 + E k2] of column c in registers;
+//            the multiplier (convection: i (v_x k_x + v_y k_y) / (nx ny)),
+//            the inverse P-point DFT and the conjugate twiddles follow in
+//            registers and the values go back where they were read;
+//   __syncthreads;
+//   stage 1 inverse: the inverse E-point DFT over k1, stored to global.
+// The packed column 0 of the tile at k_x = 0 (DC real, row-Nyquist
+// imaginary) needs no pairing of (k_y, -k_y): both columns it carries take
+// the multiplier at k_x = 0, because the Nyquist bin of k_x is zero.
+// ---------------------------------------------------------------------------
+
+template <int NY> struct ColCfg;
+template <> struct ColCfg<1024> { static constexpr int E = 32, P = 32, TW = 8; };
+template <> struct ColCfg<512> { static constexpr int E = 32, P = 16, TW = 16; };
+template <> struct ColCfg<256> { static constexpr int E = 16, P = 16, TW = 16; };
+
+template <int NY>
+__device__ __forceinline__ int cpos(int c, int l, int k1) {
+    constexpr int P = ColCfg<NY>::P, TW = ColCfg<NY>::TW, SW = TW < 16 ? 16 / TW - 1 : 0;
+    return (k1 * P + (l ^ (k1 & SW))) * TW + c;
+}
+
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(float2 *spec,
+                                                                             const GroupDesc *__restrict__ groups,
+                                                                             int ngroups,
+                                                                             const float *__restrict__ kxt,
+                                                                             const float *__restrict__ kyt,
+                                                                             const float2 *__restrict__ twc_g,
+                                                                             KP<float> P, int BOXR, int nbuf,
+                                                                             const __grid_constant__ CUtensorMap tmap,
+                                                                             int *err) {
+    using C = float2;
+    using real = float;
+    constexpr int E = ColCfg<NY>::E, PP = ColCfg<NY>::P, TW = ColCfg<NY>::TW, NT = TW * PP;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1;
+    __shared__ GroupDesc gd;
+    const int h = P.h, tid = threadIdx.x;
+    const int c = tid % TW, jl = tid / TW;
+    const size_t slot = (size_t)NY * h;
+    constexpr int tile = TW * NY;
+    SmemCursor sc{smem_raw, 0u};
+    C *twc = (C *)sc.take(NY * sizeof(C));
+    real *kxs = (real *)sc.take((size_t)(h + 1) * sizeof(real));
+    real *kys = (real *)sc.take(NY * sizeof(real));
+    C *buf0 = (C *)sc.take((size_t)tile * sizeof(C));
+    C *buf1 = nbuf > 1 ? (C *)sc.take((size_t)tile * sizeof(C)) : buf0;
+    const int ntiles = h / TW;
+    const int njobs_total = P.nrun * ngroups * ntiles;
+    const int njobs = (int)blockIdx.x < njobs_total ? (njobs_total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(twc, twc_g, NY, NT);
+    load_tab(kxs, kxt, h + 1, NT);
+    load_tab(kys, kyt, NY, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+    }
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1;
+    const real scale = P.scale;
+    for (int k = 0; k < njobs; ++k) {
+        const bool odd = k & 1;
+        uint64_t *bar = odd ? &bar1 : &bar0;
+        const int job = (int)blockIdx.x + k * (int)gridDim.x;
+        const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
+        const int g = jr / ntiles, t = jr - g * ntiles;
+        const int kx0 = t * TW;
+        if (tid == 0) gd = groups[g];
+        if (!block_wait(bar, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        C *T = odd ? buf1 : buf0;
+        // (the group's fields are read before the next job's thread 0 can
+        // overwrite gd: after this job's last block barrier only registers
+        // are used)
+        const int oslot = gd.out_slot[0];
+        const real c0 = (real)gd.c[0][0][0], c1 = (real)gd.c[0][0][1];
+        C v[E];
+        // stage 1, forward
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = T[(jl + PP * q) * TW + c];
+        SmallDFT<E, -1, C>::run(v);
+#pragma unroll
+        for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], twc[k1 * PP + jl]);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < E; ++k1) T[cpos<NY>(c, jl, k1)] = v[k1];
+        __syncthreads();
+        // stage 2: forward, multiplier, inverse, conjugate twiddles
+        {
+            const real mx = c0 * kxs[kx0 + c];
+#pragma unroll
+            for (int q = 0; q < E / PP; ++q) {
+                const int k1 = jl + PP * q;
+                C u[PP];
+#pragma unroll
+                for (int l = 0; l < PP; ++l) u[l] = T[cpos<NY>(c, l, k1)];
+                SmallDFT<PP, -1, C>::run(u);
+#pragma unroll
+                for (int k2 = 0; k2 < PP; ++k2) {
+                    const real m = (mx + c1 * kys[k1 + E * k2]) * scale;   // i m
+                    u[k2] = C{-m * u[k2].y, m * u[k2].x};
+                }
+                SmallDFT<PP, +1, C>::run(u);
+#pragma unroll
+                for (int l = 0; l < PP; ++l) T[cpos<NY>(c, l, k1)] = l == 0 ? u[l] : cmul(u[l], cconj(twc[k1 * PP + l]));
+            }
+        }
+        __syncthreads();
+        // stage 1, inverse
+#pragma unroll
+        for (int k1 = 0; k1 < E; ++k1) v[k1] = T[cpos<NY>(c, jl, k1)];
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && k + nbuf < njobs) {   // the tile buffer is free: prefetch job k + nbuf into it
+            const bool nodd = (k + nbuf) & 1;
+            kcol_issue(T, nodd ? &bar1 : &bar0, groups, k + nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
+            if (nodd) pend1 = true;
+            else pend0 = true;
+        }
+        SmallDFT<E, +1, C>::run(v);
+        C *out = spec + (size_t)run * NSLOT * slot + (size_t)oslot * slot + kx0 + c;
+#pragma unroll
+        for (int q = 0; q < E; ++q) out[(size_t)(jl + PP * q) * h] = v[q];
+    }
+}
+
+// shared memory of kcol_wr<NY> with nbuf tile buffers
+inline size_t kcol_wr_smem(int NY, int h, int nbuf) {
+    const int TW = NY == 1024 ? 8 : 16;
+    const size_t tile = (size_t)TW * NY * 8;
+    return smem_bytes({(size_t)NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, tile, nbuf > 1 ? tile : 0});
+}
+
 // shared memory of k5_wr<H>
 inline size_t k5_wr_smem(int H) {
     const int P = H == 512 ? 32 : H == 256 ? 16 : 8;

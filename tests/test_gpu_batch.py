@@ -113,14 +113,16 @@ def test_batch_runs_match_oracle(fl):
     64^2 slabs at different temperatures share one group (one launch over
     both runs), a 48 x 96 droplet has radix-3 axes, and two 128^2 spinodal
     quenches share an fp32 group beside a 96^2 fp32 slab and two 32 x 512
-    quenches (the warp-resident row kernels over two runs).  FP64 runs: the
+    quenches and two 256 x 32 quenches (the warp-resident row and column
+    kernels over two runs).  FP64 runs: the
     1e-9 bar; FP32 runs: fp32_force_bound elementwise."""
     nsteps = 3
     drop_fields, drop_kw = droplet_ragged()
     cases = [slab_case(64, 0.9, 64, 21), slab_case(64, 0.8, 64, 22),
              (drop_fields, dict(drop_kw, precision=64, integrator=3)),
              spinodal_case(128, 0.8, 32, 23), spinodal_case(128, 0.75, 32, 24), slab_case(96, 0.85, 32, 25),
-             wide_case(512, 32, 0.8, 26), wide_case(512, 32, 0.85, 27)]
+             wide_case(512, 32, 0.8, 26), wide_case(512, 32, 0.85, 27), wide_case(32, 256, 0.8, 28),
+             wide_case(32, 256, 0.9, 29)]
     with fl.Batch([fl.params(**kw) for _, kw in cases], autotune=True) as b:
         for r, (fields, _) in enumerate(cases):
             b.set_fields(r, *fields)

@@ -380,12 +380,14 @@ def test_droplet_512_precision_config(fl, precision):
         assert err < bound
 
 
-@pytest.mark.parametrize("nx,ny", [(1024, 32), (512, 48), (512, 16), (1024, 96)])
+@pytest.mark.parametrize("nx,ny", [(1024, 32), (512, 48), (512, 16), (1024, 96), (16, 1024), (32, 512), (64, 256),
+                                   (48, 1024), (96, 512)])
 def test_wide_rows_fp32(fl, nx, ny):
-    """Row widths nx = 512 and 1024, where the fp32 path runs its
-    warp-resident row kernels, on narrow grids (columns of 16 to 96, the
-    radix-3 lengths 48 and 96 included) against the oracle after 3 SSP-RK3
-    steps of a spinodal quench at T = 0.8 T_c, element by element within
+    """Row widths nx = 512 and 1024 and column lengths ny = 256, 512 and
+    1024, where the fp32 path runs its warp-resident row and column
+    kernels, on narrow grids (the other axis 16 to 96, the radix-3 lengths
+    48 and 96 included) against the oracle after 3 SSP-RK3 steps of a
+    spinodal quench at T = 0.8 T_c, element by element within
     fp32_force_bound."""
     kw = dict(nx=nx, ny=ny, a=A49, b=B21)
     fields = W.spinodal(nx, ny, RHOC49, 0.8 * TC49, amp=0.01, seed=nx + ny)

@@ -51,3 +51,34 @@ def test_real_rows_round_trip(H):
     y = np.empty(2 * H)
     y[0::2], y[1::2] = z.real, z.imag
     assert np.allclose(y, 2 * H * x)
+
+
+@pytest.mark.parametrize("NY", [1024, 512, 256])
+def test_column_tile_transform(NY):
+    """kcol_wr's index arithmetic: forward, multiplier, inverse equals
+    NY * IDFT(m DFT(x)) per column of the tile."""
+    E, P, TW = M.COLCFG[NY]
+    rng = np.random.default_rng(NY)
+    tile = rng.standard_normal((NY, TW)) + 1j * rng.standard_normal((NY, TW))
+    mult = rng.standard_normal((TW, NY)) + 1j * rng.standard_normal((TW, NY))
+    got = M.col_conv_wr(tile, NY, mult)
+    want = np.stack([np.fft.ifft(mult[c] * np.fft.fft(tile[:, c])) * NY for c in range(TW)], axis=1)
+    assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("NY", [1024, 512, 256])
+def test_column_tile_layout(NY):
+    """The swizzled positions are a permutation of the tile; the rows a
+    thread's in-place store overwrites were read by threads of its own warp
+    (so __syncwarp orders them); no bank conflicts."""
+    E, P, TW = M.COLCFG[NY]
+    assert {M.cpos(NY, c, l, k1) for c in range(TW) for l in range(P) for k1 in range(E)} == set(range(TW * NY))
+    for l in range(P):
+        for c in range(TW):
+            for k1 in range(E):
+                pos = M.cpos(NY, c, l, k1)
+                row, col = divmod(pos, TW)
+                reader_l = row % P                    # stage 1 read row l' + P t
+                assert col == c
+                assert (c + TW * reader_l) // 32 == (c + TW * l) // 32
+    assert M.worst_conflict_sets(M.col_access_sets(NY)) == 1

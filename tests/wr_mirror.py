@@ -144,3 +144,83 @@ def c2r_pre(X, H):
         if H - k != k:
             z[H - k] = (q + np.conj(p)) + 1j * ((q - np.conj(p)) * (-w))
     return z
+
+
+COLCFG = {1024: (32, 32, 8), 512: (32, 16, 16), 256: (16, 16, 16)}   # NY: (E, P, TW)
+
+
+def cpos(NY, c, l, k1):
+    E, P, TW = COLCFG[NY]
+    SW = 16 // TW - 1 if TW < 16 else 0
+    return (k1 * P + (l ^ (k1 & SW))) * TW + c
+
+
+def col_conv_wr(tile, NY, mult, rec=None):
+    """Emulates kcol_wr's transforms on a tile [NY][TW] (complex): stage 1,
+    in-place swizzled store, stage 2 with the per-element multiplier
+    mult[c][k], inverse, stage 1 inverse; returns the [NY][TW] result
+    (unnormalised: NY * IDFT(mult * DFT))."""
+    E, P, TW = COLCFG[NY]
+    T = tile.reshape(-1).astype(complex).copy()
+    tw = np.exp(-2j * np.pi * np.outer(np.arange(E), np.arange(P)) / NY)   # tw[k1, l]
+    thread = lambda c, l: c + TW * l
+    regs = {}
+    for l in range(P):
+        for c in range(TW):
+            v = np.array([T[(l + P * t) * TW + c] for t in range(E)])
+            if rec:
+                for t in range(E):
+                    rec.add(("s1load", t), thread(c, l) % 32 + 32 * 0, ((l + P * t) * TW + c, thread(c, l) // 32))
+            regs[(c, l)] = dft(v, -1) * tw[:, l]
+    for (c, l), v in regs.items():
+        for k1 in range(E):
+            T[cpos(NY, c, l, k1)] = v[k1]
+    for c in range(TW):
+        for j in range(P):
+            for q in range(E // P):
+                k1 = j + P * q
+                u = np.array([T[cpos(NY, c, l, k1)] for l in range(P)])
+                X = dft(u, -1)
+                Y = X * np.array([mult[c][k1 + E * k2] for k2 in range(P)])
+                w = dft(Y, +1) * np.conj(tw[k1, :])
+                for l in range(P):
+                    T[cpos(NY, c, l, k1)] = w[l]
+    out = np.empty((NY, TW), complex)
+    for l in range(P):
+        for c in range(TW):
+            v = np.array([T[cpos(NY, c, l, k1)] for k1 in range(E)])
+            y = dft(v, +1)
+            for t in range(E):
+                out[l + P * t, c] = y[t]
+    return out
+
+
+def col_access_sets(NY):
+    """(instruction, warp) -> {lane: word} of kcol_wr's shared-memory tile
+    accesses, for bank-conflict counting."""
+    E, P, TW = COLCFG[NY]
+    sets = {}
+    for tid in range(TW * P):
+        c, jl = tid % TW, tid // TW
+        w, lane = tid // 32, tid % 32
+        for t in range(E):
+            sets.setdefault(("s1load", t, w), {})[lane] = (jl + P * t) * TW + c
+        for k1 in range(E):
+            sets.setdefault(("s1store", k1, w), {})[lane] = cpos(NY, c, jl, k1)
+        for q in range(E // P):
+            for l in range(P):
+                sets.setdefault(("s2", q, l, w), {})[lane] = cpos(NY, c, l, jl + P * q)
+    return sets
+
+
+def worst_conflict_sets(sets):
+    worst = 1
+    for lanes in sets.values():
+        for half in (0, 1):
+            ws = {w for ln, w in lanes.items() if ln // 16 == half}
+            banks = {}
+            for w in ws:
+                banks.setdefault((2 * w) % 32, set()).add(w)
+            if banks:
+                worst = max(worst, max(len(v) for v in banks.values()))
+    return worst
