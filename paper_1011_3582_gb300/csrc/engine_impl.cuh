@@ -696,10 +696,10 @@ class EngineT : public Engine {
     // warp-resident fp32 row kernels (kernels_wr.cuh) for nx = 512, 1024:
     // their stage-1 twiddle table and launch shape
     static constexpr bool wr_ok_ = std::is_same<real, float>::value && !SPLIT;
-    bool k5wr_ = false;
+    bool k5wr_ = false, k1wr_ = false, k3wr_ = false;
     C *Tw1_ = nullptr;
-    size_t smem5w_ = 0;
-    int grid5w_ = 1;
+    size_t smem5w_ = 0, smem1w_ = 0, smem3w_ = 0;
+    int grid5w_ = 1, grid1w_ = 1, grid3w_ = 1;
     // warp-resident convection columns for ny = 256, 512, 1024
     bool colwr_ = false;
     C *Twc_ = nullptr;
@@ -1474,6 +1474,28 @@ class EngineT : public Engine {
                     grid5w_ = std::min(B_ * ny_, nb * nsm_);
                 }
             }
+            if ((h_ == 512 || h_ == 256) && Tw1_ && k3_wr_smem(h_) <= budget_) {
+                smem3w_ = k3_wr_smem(h_);
+                int nb = 0;
+                Status st = h_ == 512 ? occupancy(k3_wr<512>, NT3W, smem3w_, &nb)
+                                      : occupancy(k3_wr<256>, NT3W, smem3w_, &nb);
+                if (!st.good()) return st;
+                if (nb >= 1) {
+                    k3wr_ = true;
+                    grid3w_ = std::min(B_ * ny_, nb * nsm_);
+                }
+            }
+            if ((h_ == 512 || h_ == 256) && Tw1_ && k1_wr_smem(h_) <= budget_) {
+                smem1w_ = k1_wr_smem(h_);
+                int nb = 0;
+                Status st = h_ == 512 ? occupancy(k1_wr<512>, NT1W, smem1w_, &nb)
+                                      : occupancy(k1_wr<256>, NT1W, smem1w_, &nb);
+                if (!st.good()) return st;
+                if (nb >= 1) {
+                    k1wr_ = true;
+                    grid1w_ = std::min(B_ * ny_, nb * nsm_);
+                }
+            }
             const int TWw = ny_ == 1024 ? 8 : 16, NTw = TWw * (ny_ == 1024 ? 32 : 16);
             if (Twc_ && h_ % TWw == 0) {
                 // one or two tile buffers: the most blocks per SM, then two
@@ -1718,7 +1740,18 @@ class EngineT : public Engine {
             FFTLB_LAUNCHED("k_wait_selftest");
         }
         if (!(st = prof_begin(KK_ROW_FORWARD)).good()) return st;
-        if (SMAX1_ == 1)
+        bool k1done = false;
+        if constexpr (wr_ok_) {
+            if (k1wr_) {
+                if (h_ == 512)
+                    k1_wr<512><<<grid1w_, NT1W, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
+                else
+                    k1_wr<256><<<grid1w_, NT1W, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
+                k1done = true;
+            }
+        }
+        if (k1done) {
+        } else if (SMAX1_ == 1)
             k1_pipe<real, 1, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 2)
@@ -1737,7 +1770,17 @@ class EngineT : public Engine {
         if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
-        {
+        bool k3done = false;
+        if constexpr (wr_ok_) {
+            if (k3wr_) {
+                if (h_ == 512)
+                    k3_wr<512><<<grid3w_, NT3W, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                else
+                    k3_wr<256><<<grid3w_, NT3W, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                k3done = true;
+            }
+        }
+        if (!k3done) {
             const int ml = row_maxlr(WR3_, NT3);
             k3_pipe<real, SPLIT><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, ml == 3 ? Tr8_ : Tr_,
                                                               ml == 3 ? ntr8_ : ntr_, kp_, WR3_, ml, err_);

@@ -225,6 +225,302 @@ __device__ __forceinline__ void c2r_pre_wr(C *z, const C *Wp, int j) {
 }
 
 // ---------------------------------------------------------------------------
+// K1 (fp32, nx = 2H): moments rho, u, T (Eqs. 7-9), the level-1 fields
+// Pi = P^w - rho T (Eq. 18) and g = M/T, and the forward row transforms of
+// the 32 moving f_i and of rho, u_x, u_y, T, Pi, g, as k1_pipe, with
+// warp-resident row transforms.  Persistent over the rows of all runs;
+// per row, 32 / NG chunks of distribution rows (the first also holds the
+// rest velocity's row, which only enters the moments), NG = rows per block
+// pass (one per row group), two chunk buffers.
+// ---------------------------------------------------------------------------
+
+constexpr int NT1W = 512;
+
+template <int H>
+__global__ void __launch_bounds__(NT1W, 1) k1_wr(const float *__restrict__ f, float2 *spec, float *__restrict__ fields,
+                                                 const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
+                                                 KP<float> P, int *err) {
+    using C = float2;
+    using real = float;
+    constexpr int NX = 2 * H, NT = NT1W, NWARP = NT / 32;
+    constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
+    constexpr int NG = NWARP * RPW;                // row groups per block
+    constexpr int CH = NG + 1, NCH = NMOV / NG;    // rows per chunk buffer, chunks per row
+    constexpr int SMAX = (NX + NT - 1) / NT;
+    static_assert(NMOV % NG == 0 && NG >= 6, "chunking");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1;
+    const int nx = NX, ny = P.ny, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp * RPW + lane / PL, j = lane & (PL - 1);
+    const int rsw = PL == 8 ? ((lane / PL) & 1) : 0;
+    const size_t N = (size_t)NX * ny, slot = (size_t)ny * H;
+    SmemCursor sc{smem_raw, 0u};
+    C *tw = (C *)sc.take(H * sizeof(C));
+    C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
+    real *buf0 = (real *)sc.take((size_t)CH * NX * sizeof(real));
+    real *buf1 = (real *)sc.take((size_t)CH * NX * sizeof(real));
+    real *fb = (real *)sc.take((size_t)6 * NX * sizeof(real));   // rho, ux, uy, T, Pi, g rows
+    const int NY = P.nrun * ny;
+    const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs = nrows * NCH;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(tw, tw_g, H, NT);
+    load_tab(Wp, Wp_g, H / 2 + 1, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (njobs > 0) k1_issue(f, buf0, &bar0, 0, NCH, CH, nx, ny, N);
+        if (njobs > 1) k1_issue(f, buf1, &bar1, 1, NCH, CH, nx, ny, N);
+    }
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = njobs > 0, pend1 = njobs > 1;
+    real a0[SMAX], a1[SMAX], a2[SMAX], a3[SMAX];
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) a0[s] = a1[s] = a2[s] = a3[s] = real(0);
+    for (int jb = 0; jb < njobs; ++jb) {
+        const bool odd = jb & 1;
+        uint64_t *bar = odd ? &bar1 : &bar0;
+        const int ri = jb / NCH, c = jb - ri * NCH;
+        const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int run = yg / ny, y = yg - run * ny;
+        C *spec_r = spec + (size_t)run * NSLOT * slot;
+        real *fields_r = fields + (size_t)run * 4 * N;
+        const int i0 = c * CH, nf = min(CH, Q - i0);
+        if (!block_wait(bar, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        real *B = odd ? buf1 : buf0;
+        // moments (Eqs. 7-9): sums over this chunk's rows
+#pragma unroll 1
+        for (int r = 0; r < nf; ++r) {
+            const int i = i0 + r;
+            const real vx = VX<real>(i), vy = VY<real>(i), v2 = V2<real>(i);
+#pragma unroll
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                const real v = B[(size_t)r * NX + x];
+                a0[s] += v;
+                a1[s] += vx * v;
+                a2[s] += vy * v;
+                a3[s] += v2 * v;
+            }
+        }
+        __syncthreads();
+        // forward transforms of the chunk's moving rows: group grp takes
+        // chunk row grp + (c == 0) (the first chunk's row 0 is the rest
+        // velocity), i.e. f_i with i = i0 + that row, into slot i - 1
+        {
+            const int r = grp + (c == 0 ? 1 : 0);
+            if (r < nf) {
+                C *zr = reinterpret_cast<C *>(B) + (size_t)r * H;
+                row_fft_wr<H, -1>(zr, tw, j, rsw);
+                r2c_post_wr<H>(zr, spec_r + (size_t)(i0 + r - 1) * slot + (size_t)y * H, Wp, j);
+            }
+        }
+        if (c == NCH - 1) {
+            // the level-1 fields of this row, then their forward transforms
+#pragma unroll
+            for (int s = 0; s < SMAX; ++s) {
+                const int x = tid + s * NT;
+                const real rho = a0[s], ux = a1[s] / rho, uy = a2[s] / rho;
+                const real T = real(0.5) * (a3[s] / rho - (ux * ux + uy * uy));
+                const size_t o = (size_t)y * nx + x;
+                fields_r[o] = rho;
+                fields_r[N + o] = ux;
+                fields_r[2 * N + o] = uy;
+                fields_r[3 * N + o] = T;
+                fb[x] = rho;
+                fb[NX + x] = ux;
+                fb[2 * NX + x] = uy;
+                fb[3 * NX + x] = T;
+                fb[4 * NX + x] = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;   // Eq. 18
+                fb[5 * NX + x] = (P.K + P.H * T) / T;                                          // M / T
+                a0[s] = a1[s] = a2[s] = a3[s] = real(0);
+            }
+            __syncthreads();
+            if (grp < 6) {
+                C *zr = reinterpret_cast<C *>(fb) + (size_t)grp * H;
+                row_fft_wr<H, -1>(zr, tw, j, rsw);
+                r2c_post_wr<H>(zr, spec_r + (size_t)(SLOT_RHO + grp) * slot + (size_t)y * H, Wp, j);
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && jb + 2 < njobs) {   // job jb + 2 reuses this buffer
+            k1_issue(f, B, bar, jb + 2, NCH, CH, nx, ny, N);
+            if (odd) pend1 = true;
+            else pend0 = true;
+        }
+    }
+}
+
+// shared memory of k1_wr<H>
+inline size_t k1_wr_smem(int H) {
+    const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
+    const int CH = (NT1W / 32) * (32 / P) + 1;
+    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4,
+                       (size_t)6 * 2 * H * 4});
+}
+
+// ---------------------------------------------------------------------------
+// K3 (fp32, nx = 2H): row inverse of the 15 level-1 derivative spectra ->
+// Lambda (Eq. 19), Phi = 2 q rho T grad T (Eq. 23), the numerators of C
+// (Eq. 22) and B (Eq. 21) -> forward row transforms of Lambda_xx,
+// Lambda_xy, Lambda_yy, Phi_x, Phi_y, as k3_pipe, with warp-resident row
+// transforms.  Persistent over the rows of all runs, one row per pass, two
+// buffers (15 spectrum rows + rho, T), the next-but-one row prefetched.
+// ---------------------------------------------------------------------------
+
+constexpr int NT3W = 512;
+
+template <typename real>
+__device__ __forceinline__ void k3_issue(const typename cplx_of<real>::type *spec, const real *fields, real *dst,
+                                         uint64_t *bar, int ri, int nx, int ny, size_t N, size_t slot, int h) {
+    const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+    const int run = yg / ny, y = yg - run * ny;
+    spec += (size_t)run * NSLOT * slot;
+    fields += (size_t)run * 4 * N;
+    const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
+    mbar_expect_tx(bar, (uint32_t)(ND1 + 2) * rowbytes);
+    for (int o = 0; o < ND1; ++o)
+        bulk_g2s(dst + (size_t)o * nx, spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h, rowbytes, bar);
+    bulk_g2s(dst + (size_t)ND1 * nx, fields + (size_t)y * nx, rowbytes, bar);
+    bulk_g2s(dst + (size_t)(ND1 + 1) * nx, fields + 3 * N + (size_t)y * nx, rowbytes, bar);
+}
+
+template <int H>
+__global__ void __launch_bounds__(NT3W, 1) k3_wr(float2 *spec, const float *__restrict__ fields,
+                                                 float *__restrict__ aux, const float2 *__restrict__ tw_g,
+                                                 const float2 *__restrict__ Wp_g, KP<float> P, int *err) {
+    using C = float2;
+    using real = float;
+    constexpr int NX = 2 * H, NT = NT3W, NWARP = NT / 32;
+    constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
+    constexpr int SMAX = (NX + NT - 1) / NT;
+    constexpr int RB = ND1 + 2;   // rows per buffer
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0, bar1;
+    const int nx = NX, ny = P.ny, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp * RPW + lane / PL, j = lane & (PL - 1);
+    const int rsw = PL == 8 ? ((lane / PL) & 1) : 0;
+    const size_t N = (size_t)NX * ny, slot = (size_t)ny * H;
+    SmemCursor sc{smem_raw, 0u};
+    C *tw = (C *)sc.take(H * sizeof(C));
+    C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
+    real *buf0 = (real *)sc.take((size_t)RB * NX * sizeof(real));
+    real *buf1 = (real *)sc.take((size_t)RB * NX * sizeof(real));
+    const int NY = P.nrun * ny;
+    const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init(&bar1, 1);
+        mbar_init_fence();
+    }
+    load_tab(tw, tw_g, H, NT);
+    load_tab(Wp, Wp_g, H / 2 + 1, NT);
+    __syncthreads();
+    if (tid == 0) {
+        if (nrows > 0) k3_issue<real>(spec, fields, buf0, &bar0, 0, nx, ny, N, slot, H);
+        if (nrows > 1) k3_issue<real>(spec, fields, buf1, &bar1, 1, nx, ny, N, slot, H);
+    }
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = nrows > 0, pend1 = nrows > 1;
+    for (int ri = 0; ri < nrows; ++ri) {
+        const bool odd = ri & 1;
+        uint64_t *bar = odd ? &bar1 : &bar0;
+        const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
+        const int run = yg / ny, y = yg - run * ny;
+        C *spec_r = spec + (size_t)run * NSLOT * slot;
+        real *aux_r = aux + (size_t)run * 3 * N;
+        if (!block_wait(bar, odd ? par1 : par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            if (pend1) mbar_wait_bounded(&bar1, par1);
+            return;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        real *d = odd ? buf1 : buf0;
+        if (grp < ND1) {
+            C *zr = reinterpret_cast<C *>(d) + (size_t)grp * H;
+            c2r_pre_wr<H>(zr, Wp, j);
+            __syncwarp(group_mask<PL>());
+            row_fft_wr<H, +1>(zr, tw, j, rsw);
+        }
+        __syncthreads();
+        const real *rT = d + (size_t)ND1 * NX;
+#pragma unroll 1
+        for (int s = 0; s < SMAX; ++s) {
+            const int x = tid + s * NT;
+            const size_t o = (size_t)y * nx + x;
+            const real rho = rT[x], T = rT[NX + x];
+            const real rx = d[D_RX * NX + x], ry = d[D_RY * NX + x], lap = d[D_LAP * NX + x];
+            const real uxx = d[D_UXX * NX + x], uxy = d[D_UXY * NX + x];
+            const real uyx = d[D_UYX * NX + x], uyy = d[D_UYY * NX + x];
+            const real divx = d[D_DIVX * NX + x], divy = d[D_DIVY * NX + x];
+            const real Tx = d[D_TX * NX + x], Ty = d[D_TY * NX + x];
+            const real Pix = d[D_PIX * NX + x], Piy = d[D_PIY * NX + x];
+            const real gx = d[D_GX * NX + x], gy = d[D_GY * NX + x];
+            const real M = P.K + P.H * T;
+            const real Pi = rho * T / (real(1) - P.b * rho) - P.a * rho * rho - rho * T;
+            const real grad2 = rx * rx + ry * ry;
+            const real iso = -(rho * T * (rx * gx + ry * gy)) - M * (rho * lap + real(0.5) * grad2);   // Eq. 19
+            const real Lxx = M * rx * rx + iso, Lxy = M * rx * ry, Lyy = M * ry * ry + iso;
+            const real div = uxx + uyy;
+            const real Ldu = Lxx * uxx + Lxy * (uyx + uxy) + Lyy * uyy;
+            const real Cn = Pi * div + Ldu - P.zeta * div * div + P.a * rho * rho * div +
+                            P.K * (real(-0.5) * grad2 * div - rho * (rx * divx + ry * divy) -
+                                   (rx * (uxx * rx + uyx * ry) + ry * (uxy * rx + uyy * ry)));   // Eq. 22
+            aux_r[o] = Cn;
+            aux_r[N + o] = Pix - P.zeta * divx;   // Eq. 21 without d_b Lambda_ab
+            aux_r[2 * N + o] = Piy - P.zeta * divy;
+            const real q2 = real(2) * P.q * rho * T;   // Eq. 23
+            // rows 0..4 (same site, same thread)
+            d[0 * NX + x] = Lxx;
+            d[1 * NX + x] = Lxy;
+            d[2 * NX + x] = Lyy;
+            d[3 * NX + x] = q2 * Tx;
+            d[4 * NX + x] = q2 * Ty;
+        }
+        __syncthreads();
+        if (grp < 5) {
+            C *zr = reinterpret_cast<C *>(d) + (size_t)grp * H;
+            row_fft_wr<H, -1>(zr, tw, j, rsw);
+            r2c_post_wr<H>(zr, spec_r + (size_t)(SLOT_L2 + grp) * slot + (size_t)y * H, Wp, j);
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && ri + 2 < nrows) {
+            k3_issue<real>(spec, fields, d, bar, ri + 2, nx, ny, N, slot, H);
+            if (odd) pend1 = true;
+            else pend0 = true;
+        }
+    }
+}
+
+// shared memory of k3_wr<H>
+inline size_t k3_wr_smem(int H) {
+    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)(ND1 + 2) * 2 * H * 4,
+                       (size_t)(ND1 + 2) * 2 * H * 4});
+}
+
+// ---------------------------------------------------------------------------
 // K5 (fp32, nx = 2H): convection rows + level-2 divergences (inverse) ->
 // A, B, C, C_q (Eqs. 20-23), f^eq (Eq. 3), I (Eq. 11), BGK and the RK
 // combination (Eq. 10), as k5_pipe, with warp-resident row transforms.
