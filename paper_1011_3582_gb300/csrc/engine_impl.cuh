@@ -701,10 +701,10 @@ class EngineT : public Engine {
     size_t smem5w_ = 0, smem1w_ = 0, smem3w_ = 0;
     int grid5w_ = 1, grid1w_ = 1, grid3w_ = 1;
     // warp-resident convection columns for ny = 256, 512, 1024
-    bool colwr_ = false;
+    bool colwr_ = false, colmwr_ = false;
     C *Twc_ = nullptr;
-    size_t smemcw_ = 0;
-    int gridcw_ = 1, nbufcw_ = 1;
+    size_t smemcw_ = 0, smemcmw_ = 0;
+    int gridcw_ = 1, nbufcw_ = 1, gridcmw_ = 1;
     CUtensorMap tmap_convw_{};
     // gradient kernels (k_grad_*): column tile width and shared memory
     int TWg_ = 0;
@@ -1519,6 +1519,19 @@ class EngineT : public Engine {
                     if (!st.good()) return st;
                     colwr_ = true;
                     gridcw_ = best * nsm_;
+                    const size_t sm = kcolm_wr_smem(ny_, h_);
+                    int nb = 0;
+                    if (sm <= budget_) {
+                        st = ny_ == 1024 ? occupancy(kcolm_wr<1024>, NTw, sm, &nb)
+                           : ny_ == 512  ? occupancy(kcolm_wr<512>, NTw, sm, &nb)
+                                         : occupancy(kcolm_wr<256>, NTw, sm, &nb);
+                        if (!st.good()) return st;
+                    }
+                    if (nb > 0) {
+                        colmwr_ = true;
+                        smemcmw_ = sm;
+                        gridcmw_ = nb * nsm_;
+                    }
                 }
             }
         }
@@ -1719,6 +1732,19 @@ class EngineT : public Engine {
                     kcol_wr<256><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
                                                                       kp_, BOXR_, nbufcw_, tmap_convw_, err_);
                 FFTLB_LAUNCHED("kcol_wr");
+                return Status::ok();
+            }
+            if (level1 && colmwr_) {
+                if (ny_ == 1024)
+                    kcolm_wr<1024><<<gridcmw_, 256, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_,
+                                                                          Twc_, kp_, BOXR_, tmap_convw_, err_);
+                else if (ny_ == 512)
+                    kcolm_wr<512><<<gridcmw_, 256, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_,
+                                                                         Twc_, kp_, BOXR_, tmap_convw_, err_);
+                else
+                    kcolm_wr<256><<<gridcmw_, 256, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_,
+                                                                         Twc_, kp_, BOXR_, tmap_convw_, err_);
+                FFTLB_LAUNCHED("kcolm_wr");
                 return Status::ok();
             }
         }

@@ -893,6 +893,151 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(flo
     }
 }
 
+// Derivative column groups (level 1 and level 2): up to 2 input spectra and
+// 6 outputs per group, every output a sum of up to 2 terms M(k_x, k_y) X_in
+// with M = i (c0 k_x + c1 k_y) + (c2 k_x^2 + c3 k_y^2 + c4 k_x k_y).  Each
+// input tile takes stage 1 and stage 2 forward in place; stage 2 writes the
+// spectrum X[k1 + E k2] back where it read (l -> k2), so every thread owns
+// the spectrum values it needs.  Per output: the combination, the inverse
+// stage 2 and the conjugate twiddles into the work tile, a block barrier,
+// the inverse stage 1 and the global store, a block barrier.  The next job's
+// input tiles are fetched as soon as the last output has read them.
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(float2 *spec,
+                                                                              const GroupDesc *__restrict__ groups,
+                                                                              int ngroups,
+                                                                              const float *__restrict__ kxt,
+                                                                              const float *__restrict__ kyt,
+                                                                              const float2 *__restrict__ twc_g,
+                                                                              KP<float> P, int BOXR,
+                                                                              const __grid_constant__ CUtensorMap tmap,
+                                                                              int *err) {
+    using C = float2;
+    using real = float;
+    constexpr int E = ColCfg<NY>::E, PP = ColCfg<NY>::P, TW = ColCfg<NY>::TW, NT = TW * PP;
+    constexpr int NQ = E / PP;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar0;
+    __shared__ GroupDesc gd;
+    const int h = P.h, tid = threadIdx.x;
+    const int c = tid % TW, jl = tid / TW;
+    const size_t slot = (size_t)NY * h;
+    constexpr int tile = TW * NY;
+    SmemCursor sc{smem_raw, 0u};
+    C *twc = (C *)sc.take(NY * sizeof(C));
+    real *kxs = (real *)sc.take((size_t)(h + 1) * sizeof(real));
+    real *kys = (real *)sc.take(NY * sizeof(real));
+    C *in = (C *)sc.take((size_t)2 * tile * sizeof(C));   // input tiles 0 and 1
+    C *W = (C *)sc.take((size_t)tile * sizeof(C));        // work tile
+    const int ntiles = h / TW;
+    const int njobs_total = P.nrun * ngroups * ntiles;
+    const int njobs = (int)blockIdx.x < njobs_total ? (njobs_total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        mbar_init(&bar0, 1);
+        mbar_init_fence();
+    }
+    load_tab(twc, twc_g, NY, NT);
+    load_tab(kxs, kxt, h + 1, NT);
+    load_tab(kys, kyt, NY, NT);
+    __syncthreads();
+    if (tid == 0 && njobs > 0) kcol_issue(in, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+    uint32_t par0 = 0;
+    bool pend0 = njobs > 0;
+    const real scale = P.scale;
+    for (int k = 0; k < njobs; ++k) {
+        const int job = (int)blockIdx.x + k * (int)gridDim.x;
+        const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
+        const int g = jr / ntiles, t = jr - g * ntiles;
+        const int kx0 = t * TW;
+        if (tid == 0) gd = groups[g];
+        if (!block_wait(&bar0, par0, err)) {
+            if (pend0) mbar_wait_bounded(&bar0, par0);
+            return;
+        }
+        par0 ^= 1;
+        pend0 = false;
+        const int nin = gd.nin, nout = gd.nout;
+        const real ax = kxs[kx0 + c];
+        // forward transforms of the inputs, in place
+        for (int s = 0; s < nin; ++s) {
+            C *T = in + (size_t)s * tile;
+            C v[E];
+#pragma unroll
+            for (int q = 0; q < E; ++q) v[q] = T[(jl + PP * q) * TW + c];
+            SmallDFT<E, -1, C>::run(v);
+#pragma unroll
+            for (int k1 = 1; k1 < E; ++k1) v[k1] = cmul(v[k1], twc[k1 * PP + jl]);
+            __syncwarp();
+#pragma unroll
+            for (int k1 = 0; k1 < E; ++k1) T[cpos<NY>(c, jl, k1)] = v[k1];
+        }
+        __syncthreads();
+        for (int s = 0; s < nin; ++s) {
+            C *T = in + (size_t)s * tile;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int k1 = jl + PP * q;
+                C u[PP];
+#pragma unroll
+                for (int l = 0; l < PP; ++l) u[l] = T[cpos<NY>(c, l, k1)];
+                SmallDFT<PP, -1, C>::run(u);
+#pragma unroll
+                for (int k2 = 0; k2 < PP; ++k2) T[cpos<NY>(c, k2, k1)] = u[k2];
+            }
+        }
+        // (each thread reads back only its own spectrum values below)
+        for (int o = 0; o < nout; ++o) {
+            const int two = gd.nterm[o] > 1;
+            const C *X0 = in + (size_t)gd.term_in[o][0] * tile;
+            const C *X1 = in + (size_t)gd.term_in[o][1] * tile;
+            const real p0 = (real)gd.c[o][0][0], p1 = (real)gd.c[o][0][1], p2 = (real)gd.c[o][0][2],
+                       p3 = (real)gd.c[o][0][3], p4 = (real)gd.c[o][0][4];
+            const real q0 = (real)gd.c[o][1][0], q1 = (real)gd.c[o][1][1], q2 = (real)gd.c[o][1][2],
+                       q3 = (real)gd.c[o][1][3], q4 = (real)gd.c[o][1][4];
+            const int oslot = gd.out_slot[o];
+            const bool last = o == nout - 1;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int k1 = jl + PP * q;
+                C u[PP];
+#pragma unroll
+                for (int k2 = 0; k2 < PP; ++k2) {
+                    const int pos = cpos<NY>(c, k2, k1);
+                    const real ay = kys[k1 + E * k2];
+                    C acc = mult_apply<real>(p0, p1, p2, p3, p4, ax, ay, X0[pos]);
+                    if (two) acc = cadd(acc, mult_apply<real>(q0, q1, q2, q3, q4, ax, ay, X1[pos]));
+                    u[k2] = cscale(acc, scale);
+                }
+                SmallDFT<PP, +1, C>::run(u);
+#pragma unroll
+                for (int l = 0; l < PP; ++l)
+                    W[cpos<NY>(c, l, k1)] = l == 0 ? u[l] : cmul(u[l], cconj(twc[k1 * PP + l]));
+            }
+            if (last) fence_proxy_async();
+            __syncthreads();
+            if (last && tid == 0 && k + 1 < njobs) {   // the input tiles are free: fetch the next job's
+                kcol_issue(in, &bar0, groups, k + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+                pend0 = true;
+            }
+            C v[E];
+#pragma unroll
+            for (int k1 = 0; k1 < E; ++k1) v[k1] = W[cpos<NY>(c, jl, k1)];
+            SmallDFT<E, +1, C>::run(v);
+            C *out = spec + (size_t)run * NSLOT * slot + (size_t)oslot * slot + kx0 + c;
+#pragma unroll
+            for (int q = 0; q < E; ++q) out[(size_t)(jl + PP * q) * h] = v[q];
+            __syncthreads();   // the work tile is rewritten by the next output
+        }
+    }
+}
+
+// shared memory of kcolm_wr<NY>
+inline size_t kcolm_wr_smem(int NY, int h) {
+    const int TW = NY == 1024 ? 8 : 16;
+    const size_t tile = (size_t)TW * NY * 8;
+    return smem_bytes({(size_t)NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, 2 * tile, tile});
+}
+
 // shared memory of kcol_wr<NY> with nbuf tile buffers
 inline size_t kcol_wr_smem(int NY, int h, int nbuf) {
     const int TW = NY == 1024 ? 8 : 16;
