@@ -1016,15 +1016,19 @@ class EngineT : public Engine {
             FFTLB_CU(cudaMemcpy(Tw1_, t1.data(), t1.size() * sizeof(C), cudaMemcpyHostToDevice));
         }
         if (wr_ok_ && (ny_ == 1024 || ny_ == 512 || ny_ == 256)) {
-            // twc[k1 P + l] = exp(-2 pi i l k1 / ny) for the column configuration of ny
+            // twc[k1 P + l] = exp(-2 pi i l k1 / ny) for the column configuration of
+            // ny, followed by the same values ordered [l][k1] (twc[ny + l E + k1])
             const int P = ny_ == 1024 ? 32 : 16, E = ny_ / P;
-            std::vector<C> t1((size_t)ny_);
+            std::vector<C> t1((size_t)2 * ny_);
             const long double pi = 3.141592653589793238462643383279502884L;
             for (int k1 = 0; k1 < E; ++k1)
                 for (int l = 0; l < P; ++l) {
                     const long double a = 2.0L * pi * (long double)(l * k1) / (long double)ny_;
-                    t1[(size_t)k1 * P + l].x = (real)cosl(a);
-                    t1[(size_t)k1 * P + l].y = (real)(-sinl(a));
+                    C w;
+                    w.x = (real)cosl(a);
+                    w.y = (real)(-sinl(a));
+                    t1[(size_t)k1 * P + l] = w;
+                    t1[(size_t)ny_ + (size_t)l * E + k1] = w;
                 }
             if (!(st = dalloc(&Twc_, t1.size())).good()) return st;
             FFTLB_CU(cudaMemcpy(Twc_, t1.data(), t1.size() * sizeof(C), cudaMemcpyHostToDevice));
@@ -1499,8 +1503,13 @@ class EngineT : public Engine {
             const int TWw = ny_ == 1024 ? 8 : 16, NTw = TWw * (ny_ == 1024 ? 32 : 16);
             if (Twc_ && h_ % TWw == 0) {
                 // one or two tile buffers: the most blocks per SM, then two
+                // (FFTLB_COLWR_NBUF fixes the count at build time)
                 int best = 0;
+#ifdef FFTLB_COLWR_NBUF
+                for (int nb2 = FFTLB_COLWR_NBUF; nb2 == FFTLB_COLWR_NBUF; --nb2) {
+#else
                 for (int nb2 = 2; nb2 >= 1; --nb2) {
+#endif
                     const size_t sm = kcol_wr_smem(ny_, h_, nb2);
                     if (sm > budget_) continue;
                     int nb = 0;

@@ -404,6 +404,19 @@ __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDes
     }
 }
 
+// L2 prefetch of the tiles kcol_issue would load for job k
+__device__ __forceinline__ void kcol_prefetch(const GroupDesc *groups, int k, int ntiles, int ngroups, int TW, int ny,
+                                              int BOXR, const CUtensorMap *tmap) {
+    const int job = (int)blockIdx.x + k * (int)gridDim.x;
+    const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
+    const int g = jr / ntiles, t = jr - g * ntiles;
+    const GroupDesc *G = groups + g;
+    for (int s = 0; s < G->nin; ++s) {
+        const int sl = run * NSLOT + G->in_slot[s];
+        for (int r0 = 0; r0 < ny; r0 += BOXR) tma_prefetch_2d(tmap, 2 * t * TW, sl * ny + r0);
+    }
+}
+
 // MULTI = false: every group has one input and one output in place
 // (convection); MULTI = true: up to 2 inputs and several outputs.
 template <typename real, bool MULTI, bool TC = false>

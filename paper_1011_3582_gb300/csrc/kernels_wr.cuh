@@ -723,6 +723,18 @@ __global__ void __launch_bounds__(NT5W, 1) k5_wr(const float2 *spec, const float
         }
         fence_proxy_async();
         __syncthreads();
+        if (tid == 0 && jb + 1 < njobs) {
+            // the next job's distribution rows (current and, for RK stages 2
+            // and 3, base state) into L2 ahead of its epilogue's loads
+            const int nri = (jb + 1) / NCH, nc = (jb + 1) - nri * NCH;
+            const int nyg = (int)blockIdx.x + nri * (int)gridDim.x;
+            const int nrun = nyg / ny, ny_ = nyg - nrun * ny;
+            const size_t no = (size_t)nrun * Q * N + (size_t)(1 + nc * CH) * N + (size_t)ny_ * nx;
+            for (int r = 0; r < CH; ++r) {
+                bulk_prefetch_l2(fcur + no + (size_t)r * N, (uint32_t)(NX * sizeof(real)));
+                if (with_base) bulk_prefetch_l2(fbase + no + (size_t)r * N, (uint32_t)(NX * sizeof(real)));
+            }
+        }
         if (tid == 0) {
             if (jb + 2 < njobs) {
                 const bool nodd = jb & 1;   // chunk jb + 2 reuses this buffer
@@ -793,7 +805,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(flo
     const size_t slot = (size_t)NY * h;
     constexpr int tile = TW * NY;
     SmemCursor sc{smem_raw, 0u};
-    C *twc = (C *)sc.take(NY * sizeof(C));
+    C *twc = (C *)sc.take((size_t)2 * NY * sizeof(C));   // [k1][l] (stage 1), then [l][k1] (stage 2)
+    const C *twt = twc + NY;
     real *kxs = (real *)sc.take((size_t)(h + 1) * sizeof(real));
     real *kys = (real *)sc.take(NY * sizeof(real));
     C *buf0 = (C *)sc.take((size_t)tile * sizeof(C));
@@ -806,13 +819,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(flo
         mbar_init(&bar1, 1);
         mbar_init_fence();
     }
-    load_tab(twc, twc_g, NY, NT);
+    load_tab(twc, twc_g, 2 * NY, NT);
     load_tab(kxs, kxt, h + 1, NT);
     load_tab(kys, kyt, NY, NT);
     __syncthreads();
     if (tid == 0) {
         if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
         if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (njobs > nbuf) kcol_prefetch(groups, nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
     }
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1;
@@ -871,7 +885,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(flo
                 }
                 SmallDFT<PP, +1, C>::run(u);
 #pragma unroll
-                for (int l = 0; l < PP; ++l) T[cpos<NY>(c, l, k1)] = l == 0 ? u[l] : cmul(u[l], cconj(twc[k1 * PP + l]));
+                for (int l = 0; l < PP; ++l) T[cpos<NY>(c, l, k1)] = l == 0 ? u[l] : cmul(u[l], cconj(twt[l * E + k1]));
             }
         }
         __syncthreads();
@@ -885,6 +899,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(flo
             kcol_issue(T, nodd ? &bar1 : &bar0, groups, k + nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
             if (nodd) pend1 = true;
             else pend0 = true;
+            // and the job after it into L2, so that its copy finds the tiles there
+            if (k + nbuf + 1 < njobs) kcol_prefetch(groups, k + nbuf + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
         }
         SmallDFT<E, +1, C>::run(v);
         C *out = spec + (size_t)run * NSLOT * slot + (size_t)oslot * slot + kx0 + c;
@@ -924,7 +940,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
     const size_t slot = (size_t)NY * h;
     constexpr int tile = TW * NY;
     SmemCursor sc{smem_raw, 0u};
-    C *twc = (C *)sc.take(NY * sizeof(C));
+    C *twc = (C *)sc.take((size_t)2 * NY * sizeof(C));   // [k1][l] (stage 1), then [l][k1] (stage 2)
+    const C *twt = twc + NY;
     real *kxs = (real *)sc.take((size_t)(h + 1) * sizeof(real));
     real *kys = (real *)sc.take(NY * sizeof(real));
     C *in = (C *)sc.take((size_t)2 * tile * sizeof(C));   // input tiles 0 and 1
@@ -936,11 +953,12 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
         mbar_init(&bar0, 1);
         mbar_init_fence();
     }
-    load_tab(twc, twc_g, NY, NT);
+    load_tab(twc, twc_g, 2 * NY, NT);
     load_tab(kxs, kxt, h + 1, NT);
     load_tab(kys, kyt, NY, NT);
     __syncthreads();
     if (tid == 0 && njobs > 0) kcol_issue(in, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+    if (tid == 0 && njobs > 1) kcol_prefetch(groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
     uint32_t par0 = 0;
     bool pend0 = njobs > 0;
     const real scale = P.scale;
@@ -1011,13 +1029,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
                 SmallDFT<PP, +1, C>::run(u);
 #pragma unroll
                 for (int l = 0; l < PP; ++l)
-                    W[cpos<NY>(c, l, k1)] = l == 0 ? u[l] : cmul(u[l], cconj(twc[k1 * PP + l]));
+                    W[cpos<NY>(c, l, k1)] = l == 0 ? u[l] : cmul(u[l], cconj(twt[l * E + k1]));
             }
             if (last) fence_proxy_async();
             __syncthreads();
             if (last && tid == 0 && k + 1 < njobs) {   // the input tiles are free: fetch the next job's
                 kcol_issue(in, &bar0, groups, k + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
                 pend0 = true;
+                if (k + 2 < njobs) kcol_prefetch(groups, k + 2, ntiles, ngroups, TW, NY, BOXR, &tmap);
             }
             C v[E];
 #pragma unroll
@@ -1035,14 +1054,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
 inline size_t kcolm_wr_smem(int NY, int h) {
     const int TW = NY == 1024 ? 8 : 16;
     const size_t tile = (size_t)TW * NY * 8;
-    return smem_bytes({(size_t)NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, 2 * tile, tile});
+    return smem_bytes({(size_t)2 * NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, 2 * tile, tile});
 }
 
 // shared memory of kcol_wr<NY> with nbuf tile buffers
 inline size_t kcol_wr_smem(int NY, int h, int nbuf) {
     const int TW = NY == 1024 ? 8 : 16;
     const size_t tile = (size_t)TW * NY * 8;
-    return smem_bytes({(size_t)NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, tile, nbuf > 1 ? tile : 0});
+    return smem_bytes({(size_t)2 * NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, tile, nbuf > 1 ? tile : 0});
 }
 
 // shared memory of k5_wr<H>

@@ -210,6 +210,13 @@ def col_access_sets(NY):
         for q in range(E // P):
             for l in range(P):
                 sets.setdefault(("s2", q, l, w), {})[lane] = cpos(NY, c, l, jl + P * q)
+        # twiddle tables (8-byte words from a separate base): stage 1 reads
+        # twc[k1 P + l], stage 2 reads twt[l E + k1]
+        for k1 in range(1, E):
+            sets.setdefault(("tw1", k1, w), {})[lane] = 10 ** 6 + k1 * P + jl
+        for q in range(E // P):
+            for l in range(1, P):
+                sets.setdefault(("tw2", q, l, w), {})[lane] = 2 * 10 ** 6 + l * E + jl + P * q
     return sets
 
 
