@@ -66,6 +66,7 @@ static __constant__ float c_vxf[Q], c_vyf[Q], c_v2f[Q];
 static __constant__ int c_ring[Q];
 static __constant__ double c_Fk[4][4];    // F_k = T (c3 + T (c2 + T (c1 + T c0)))
 static __constant__ float c_Fkf[4][4];
+static __constant__ float c_Fkl[4][4];    // fp32 remainders: c_Fk - c_Fkf
 
 // the live engines of this translation unit and their velocity set
 struct VelocitySetOwner {
@@ -147,12 +148,41 @@ __device__ void rows_c2r(C *buf, int h, int nrows, const C *Wr, const C *Wp) {
     fft_rows<+1>(buf, h, nrows, Wr);
 }
 
+// Weight F_k(T) of ring k (Eq. 4) as T (c3 + T (c2 + T (c1 + T c0))).  fp64:
+// Horner.  fp32: the compensated Horner scheme of Graillat, Langlois and
+// Louvet (2005), with the coefficients as fp32 pairs hi + lo: every step's
+// rounding errors (TwoProd through fma, TwoSum) are carried in a second
+// accumulator and added at the end, so the result is accurate to about one
+// ulp even where the polynomial cancels (F_4 near T = 0.43 has condition
+// number 1.6e4).  Plain fp32 Horner there is off by up to 4e-3 relative, an
+// error of fixed sign at a fixed T that the BGK term feeds into f every
+// step: a steady drift of mass and energy in long fp32 runs.
+template <typename real> __device__ __forceinline__ real weight_Fk(int k, real T);
+template <> __device__ __forceinline__ double weight_Fk<double>(int k, double T) {
+    return T * (c_Fk[k][3] + T * (c_Fk[k][2] + T * (c_Fk[k][1] + T * c_Fk[k][0])));
+}
+// (the error-free transformations use __fmul_rn / __fadd_rn / __fsub_rn,
+// which the compiler never contracts into an fma)
+template <> __device__ __forceinline__ float weight_Fk<float>(int k, float T) {
+    float s = c_Fkf[k][0], c = c_Fkl[k][0];
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+        const float p = __fmul_rn(s, T), pe = fmaf(s, T, -p);     // TwoProd(s, T)
+        const float a = c_Fkf[k][j];
+        const float sn = __fadd_rn(p, a), z = __fsub_rn(sn, p);   // TwoSum(p, a)
+        const float se = __fadd_rn(__fsub_rn(p, __fsub_rn(sn, z)), __fsub_rn(a, z));
+        c = fmaf(c, T, pe + se + c_Fkl[k][j]);
+        s = sn;
+    }
+    return T * (s + c);
+}
+
 template <typename real>
 __device__ __forceinline__ void weights_Fk(real T, real F[5]) {
     real s = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        real v = T * (FKC<real>(k, 3) + T * (FKC<real>(k, 2) + T * (FKC<real>(k, 1) + T * FKC<real>(k, 0))));
+        const real v = weight_Fk<real>(k, T);
         F[k + 1] = v;
         s += v;
     }
@@ -863,7 +893,7 @@ class EngineT : public Engine {
         // Eq. 4: F_k = [48 T^4 - 6 s1 T^3 + s2 T^2 - s3 T / 4] / [v_k^2 prod_l (v_k^2 - o_l)],
         // o_l = v_{k+l}^2 with the cyclic index of Eq. 6
         double Fk[4][4];
-        float Fkf[4][4];
+        float Fkf[4][4], Fkl[4][4];
         for (int k = 0; k < 4; ++k) {
             double o[3];
             for (int l = 1; l <= 3; ++l) o[l - 1] = speeds[(k + l) % 4] * speeds[(k + l) % 4];
@@ -874,7 +904,10 @@ class EngineT : public Engine {
             Fk[k][1] = -6.0 * (o[0] + o[1] + o[2]) / den;
             Fk[k][2] = (o[0] * o[1] + o[1] * o[2] + o[2] * o[0]) / den;
             Fk[k][3] = -o[0] * o[1] * o[2] / (4.0 * den);
-            for (int j = 0; j < 4; ++j) Fkf[k][j] = (float)Fk[k][j];
+            for (int j = 0; j < 4; ++j) {
+                Fkf[k][j] = (float)Fk[k][j];
+                Fkl[k][j] = (float)(Fk[k][j] - (double)Fkf[k][j]);
+            }
         }
         FFTLB_CU(cudaMemcpyToSymbol(c_vx, vx, sizeof vx));
         FFTLB_CU(cudaMemcpyToSymbol(c_vy, vy, sizeof vy));
@@ -885,6 +918,7 @@ class EngineT : public Engine {
         FFTLB_CU(cudaMemcpyToSymbol(c_ring, ring, sizeof ring));
         FFTLB_CU(cudaMemcpyToSymbol(c_Fk, Fk, sizeof Fk));
         FFTLB_CU(cudaMemcpyToSymbol(c_Fkf, Fkf, sizeof Fkf));
+        FFTLB_CU(cudaMemcpyToSymbol(c_Fkl, Fkl, sizeof Fkl));
         memcpy(vx_, vx, sizeof vx);
         memcpy(vy_, vy, sizeof vy);
         return Status::ok();
@@ -1276,7 +1310,8 @@ class EngineT : public Engine {
     // nbuf staged tiles of NIN inputs, NIN padded work tiles
     size_t col_smem(bool multi, int tw, int nbuf) const {
         const size_t cs = sizeof(C), rs = sizeof(real), pny = (size_t)padded_len(ny_);
-        const size_t tile = (size_t)tw * ny_ * cs, ptile = (size_t)tw * pny * cs, kt = (h_ + 1 + ny_) * rs;
+        // staged input tiles are placed at 128-byte strides (tile_stride)
+        const size_t tile = tile_stride<C>(tw, ny_) * cs, ptile = (size_t)tw * pny * cs, kt = (h_ + 1 + ny_) * rs;
         const size_t nin = multi ? 2 : 1;
         return nbuf > 1 ? (multi ? smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, nin * tile, ptile, ptile})
                                  : smem_bytes({ny_ * cs, ntc_ * cs, kt, nin * tile, nin * tile, ptile}))
@@ -1291,6 +1326,10 @@ class EngineT : public Engine {
         return smem_bytes({h_ * cs, h_ * cs, ntrmax() * cs, head, nhb > 1 ? head : 0, chunk, nbuf > 1 ? chunk : 0,
                            (size_t)std::max(ch, 3) * ph * cs});
     }
+    // A column tile of width tw is staged as ny / BOXR_ tensor boxes of BOXR_
+    // rows; every box needs a 128-byte aligned shared-memory destination
+    // (the input tiles themselves sit at 128-byte strides, tile_stride).
+    bool boxes_aligned(int tw) const { return ny_ <= BOXR_ || ((size_t)BOXR_ * tw * sizeof(C)) % 128 == 0; }
     // buffers for a column tile width: two unless one gives more blocks per SM
     Status col_nbuf(bool multi, int tw, int *nbuf, size_t *sm, int *grid) {
         int best = -1;
@@ -1389,6 +1428,7 @@ class EngineT : public Engine {
             for (int tw = 8; tw >= 1; tw >>= 1) {
                 if (h_ % tw) continue;
                 if ((2 * tw * rs) % 16) continue;   // tensor box row: whole 16-byte units
+                if (!boxes_aligned(tw)) continue;
                 for (int nbuf = 2; nbuf >= 1; --nbuf) {
                     int nb = 0;
                     const size_t sm = col_smem(multi, tw, nbuf);
@@ -1603,7 +1643,10 @@ class EngineT : public Engine {
         const size_t ph = (size_t)padded_len(h_), pny = (size_t)padded_len(ny_);
         const int twc = t[0] ? t[0] : TWc_, twl = t[1] ? t[1] : TWl_, ch1 = t[2] ? t[2] : CH1_;
         const int ch5 = t[3] ? t[3] : CH5_, nhb = t[4] ? t[4] : NHB5_;
-        auto twok = [&](int tw) { return tw >= 1 && tw <= 8 && (tw & (tw - 1)) == 0 && h_ % tw == 0 && (2 * tw * rs) % 16 == 0; };
+        auto twok = [&](int tw) {
+            return tw >= 1 && tw <= 8 && (tw & (tw - 1)) == 0 && h_ % tw == 0 && (2 * tw * rs) % 16 == 0 &&
+                   boxes_aligned(tw);
+        };
         if (!twok(twc) || !twok(twl) || ch1 < 6 || ch1 > 8 || ch5 < 2 || ch5 > CHMAX5 || (ch5 & 1) || nhb < 1 || nhb > 2)
             return Status::err(FFTLB_ERR_ARG, "tuning parameters out of range");
         const size_t sm1 = smem_bytes({h_ * cs, h_ * cs, ntr_ * cs, (size_t)ch1 * nx_ * rs, (size_t)ch1 * nx_ * rs, ch1 * ph * cs});

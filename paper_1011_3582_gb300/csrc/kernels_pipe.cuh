@@ -387,6 +387,15 @@ template <typename real> struct GroupMult {
     }
 };
 
+// Elements between consecutive staged input tiles of TW x ny values: the
+// tile size rounded up to 128 bytes, the alignment a tensor copy needs for
+// its shared-memory destination.
+template <typename C>
+__host__ __device__ __forceinline__ size_t tile_stride(int TW, int ny) {
+    const size_t bytes = ((size_t)TW * ny * sizeof(C) + 127) & ~(size_t)127;
+    return bytes / sizeof(C);
+}
+
 template <typename C>
 __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDesc *groups, int k, int ntiles,
                                            int ngroups, int TW, int ny, int BOXR, const CUtensorMap *tmap) {
@@ -400,7 +409,7 @@ __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDes
     for (int s = 0; s < nin; ++s) {
         const int sl = run * NSLOT + G->in_slot[s];   // the tensor spans the arenas of all runs
         for (int r0 = 0; r0 < ny; r0 += BOXR)
-            tma_load_2d(dst + (size_t)s * tile + (size_t)r0 * TW, tmap, 2 * t * TW, sl * ny + r0, bar);
+            tma_load_2d(dst + (size_t)s * tile_stride<C>(TW, ny) + (size_t)r0 * TW, tmap, 2 * t * TW, sl * ny + r0, bar);
     }
 }
 
@@ -446,10 +455,11 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
     C *Tc = (C *)sc.take(ntc * sizeof(C));
     real *kxs = (real *)sc.take((size_t)(h + 1 + ny) * sizeof(real));   // k_x then k_y tables
     real *kys = kxs + h + 1;
-    C *buf0 = (C *)sc.take((size_t)NIN * tile * sizeof(C));
+    const size_t tstr = tile_stride<C>(TW, ny);   // input s of a job at buf + s tstr
+    C *buf0 = (C *)sc.take((size_t)NIN * tstr * sizeof(C));
     // nbuf = 2: double-buffered (job k + 2 prefetched while job k + 1 runs);
     // nbuf = 1: one buffer (job k + 1 loaded after job k), for two blocks per SM
-    C *buf1 = nbuf > 1 ? (C *)sc.take((size_t)NIN * tile * sizeof(C)) : buf0;
+    C *buf1 = nbuf > 1 ? (C *)sc.take((size_t)NIN * tstr * sizeof(C)) : buf0;
     C *wk0 = (C *)sc.take((size_t)ptile * sizeof(C));
     C *wk1 = MULTI ? (C *)sc.take((size_t)ptile * sizeof(C)) : nullptr;
     const Lay lt{1, TW, 0}, lw{1, TW, 1};   // staged tile / padded work tile
@@ -531,7 +541,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 gout[(size_t)e * h + c] = R[lr(c, e)];
             }
         } else {
-            C *in1 = in0 + tile;
+            C *in1 = in0 + tstr;
             if (pow2ny && kx0 != 0 && (ilog2(ny) & 3) != 0) {   // last pass radix <= 8
                 // inputs: forward passes 1 .. L-1 (X0 in {in0, wk0}, X1 in
                 // {in1, wk1}); each output: one fused pass into the free pair
@@ -940,7 +950,7 @@ __global__ void __launch_bounds__(KCfg<real, KS_K5>::NT, KCfg<real, KS_K5>::MINB
                 const real rho = H[3 * nx + x], ux = H[4 * nx + x], uy = H[5 * nx + x], T = H[6 * nx + x];
                 const real iT = H[8 * nx + x];
                 const real e0 = H[x], e1x = H[nx + x], e1y = H[2 * nx + x], CC = H[7 * nx + x];
-                const real Fk = T * (FKC<real>(k, 3) + T * (FKC<real>(k, 2) + T * (FKC<real>(k, 1) + T * FKC<real>(k, 0))));   // Eq. 4
+                const real Fk = weight_Fk<real>(k, T);   // Eq. 4
                 const real qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
                 const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
                 const real p3 = iT * iT * iT * (real(1) / real(6)), p4 = iT * iT * iT * iT * (real(1) / real(24));

@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(NT5W, 1) k5_wr(const float2 *spec, const float
                 const real rho = Hd[3 * nx + x], ux = Hd[4 * nx + x], uy = Hd[5 * nx + x], T = Hd[6 * nx + x];
                 const real iT = Hd[8 * nx + x];
                 const real e0 = Hd[x], e1x = Hd[nx + x], e1y = Hd[2 * nx + x], CC = Hd[7 * nx + x];
-                const real Fk = T * (FKC<real>(k, 3) + T * (FKC<real>(k, 2) + T * (FKC<real>(k, 1) + T * FKC<real>(k, 0))));   // Eq. 4
+                const real Fk = weight_Fk<real>(k, T);   // Eq. 4
                 const real qq = real(0.5) * (ux * ux + uy * uy) * iT, om = real(1) - qq;
                 const real p0 = om + real(0.5) * qq * qq, p1 = om * iT, p2 = real(0.5) * om * iT * iT;
                 const real p3 = iT * iT * iT * (real(1) / real(6)), p4 = iT * iT * iT * iT * (real(1) / real(24));

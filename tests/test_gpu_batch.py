@@ -114,7 +114,8 @@ def test_batch_runs_match_oracle(fl):
     both runs), a 48 x 96 droplet has radix-3 axes, and two 128^2 spinodal
     quenches share an fp32 group beside a 96^2 fp32 slab and two 32 x 512
     quenches and two 256 x 32 quenches (the warp-resident row and column
-    kernels over two runs).  FP64 runs: the
+    kernels over two runs), and two 4 x 512 quenches, whose 4-row columns
+    the autotuner tries at tile widths with sub-128-byte tiles.  FP64 runs: the
     1e-9 bar; FP32 runs: fp32_force_bound elementwise."""
     nsteps = 3
     drop_fields, drop_kw = droplet_ragged()
@@ -122,7 +123,7 @@ def test_batch_runs_match_oracle(fl):
              (drop_fields, dict(drop_kw, precision=64, integrator=3)),
              spinodal_case(128, 0.8, 32, 23), spinodal_case(128, 0.75, 32, 24), slab_case(96, 0.85, 32, 25),
              wide_case(512, 32, 0.8, 26), wide_case(512, 32, 0.85, 27), wide_case(32, 256, 0.8, 28),
-             wide_case(32, 256, 0.9, 29)]
+             wide_case(32, 256, 0.9, 29), wide_case(512, 4, 0.85, 30), wide_case(512, 4, 0.9, 31)]
     with fl.Batch([fl.params(**kw) for _, kw in cases], autotune=True) as b:
         for r, (fields, _) in enumerate(cases):
             b.set_fields(r, *fields)
