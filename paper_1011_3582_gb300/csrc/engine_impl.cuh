@@ -734,7 +734,7 @@ class EngineT : public Engine {
     bool colwr_ = false, colmwr_ = false;
     C *Twc_ = nullptr;
     size_t smemcw_ = 0, smemcmw_ = 0;
-    int gridcw_ = 1, nbufcw_ = 1, gridcmw_ = 1;
+    int gridcw_ = 1, nbufcw_ = 1, gridcmw_ = 1, ntcw_ = 256;
     CUtensorMap tmap_convw_{};
     // gradient kernels (k_grad_*): column tile width and shared memory
     int TWg_ = 0;
@@ -1035,9 +1035,9 @@ class EngineT : public Engine {
         if (ntr_) FFTLB_CU(cudaMemcpy(Tr_, tr.data(), tr.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntr8_) FFTLB_CU(cudaMemcpy(Tr8_, tr8.data(), tr8.size() * sizeof(C), cudaMemcpyHostToDevice));
         if (ntc_) FFTLB_CU(cudaMemcpy(Tc_, tc.data(), tc.size() * sizeof(C), cudaMemcpyHostToDevice));
-        if (wr_ok_ && (h_ == 512 || h_ == 256)) {
+        if (wr_ok_ && (h_ == 512 || h_ == 256 || h_ == 128)) {
             // tw[k1 P + l] = exp(-2 pi i l k1 / h) for the row configuration of h
-            const int P = h_ == 512 ? 32 : 16, E = h_ / P;
+            const int P = h_ == 512 ? 32 : h_ == 256 ? 16 : 8, E = h_ / P;
             std::vector<C> t1((size_t)h_);
             const long double pi = 3.141592653589793238462643383279502884L;
             for (int k1 = 0; k1 < E; ++k1)
@@ -1049,10 +1049,10 @@ class EngineT : public Engine {
             if (!(st = dalloc(&Tw1_, t1.size())).good()) return st;
             FFTLB_CU(cudaMemcpy(Tw1_, t1.data(), t1.size() * sizeof(C), cudaMemcpyHostToDevice));
         }
-        if (wr_ok_ && (ny_ == 1024 || ny_ == 512 || ny_ == 256)) {
+        if (wr_ok_ && (ny_ == 1024 || ny_ == 512 || ny_ == 256 || ny_ == 128)) {
             // twc[k1 P + l] = exp(-2 pi i l k1 / ny) for the column configuration of
             // ny, followed by the same values ordered [l][k1] (twc[ny + l E + k1])
-            const int P = ny_ == 1024 ? 32 : 16, E = ny_ / P;
+            const int P = col_p_host(ny_), E = ny_ / P;
             std::vector<C> t1((size_t)2 * ny_);
             const long double pi = 3.141592653589793238462643383279502884L;
             for (int k1 = 0; k1 < E; ++k1)
@@ -1507,40 +1507,44 @@ class EngineT : public Engine {
     // 1024, and its shared memory fits)
     Status configure_wr() {
         if constexpr (wr_ok_) {
-            if ((h_ == 512 || h_ == 256) && Tw1_ && k5_wr_smem(h_) <= budget_) {
+            const bool rows = (h_ == 512 || h_ == 256 || h_ == 128) && Tw1_;
+            const int NTr = nt_wr_host(h_);
+            int nb = 0;
+            Status st;
+            if (rows && k5_wr_smem(h_) <= budget_) {
                 smem5w_ = k5_wr_smem(h_);
-                int nb = 0;
-                Status st = h_ == 512 ? occupancy(k5_wr<512>, NT5W, smem5w_, &nb)
-                                      : occupancy(k5_wr<256>, NT5W, smem5w_, &nb);
+                st = h_ == 512 ? occupancy(k5_wr<512>, NTr, smem5w_, &nb)
+                   : h_ == 256 ? occupancy(k5_wr<256>, NTr, smem5w_, &nb)
+                               : occupancy(k5_wr<128>, NTr, smem5w_, &nb);
                 if (!st.good()) return st;
                 if (nb >= 1) {
                     k5wr_ = true;
                     grid5w_ = std::min(B_ * ny_, nb * nsm_);
                 }
             }
-            if ((h_ == 512 || h_ == 256) && Tw1_ && k3_wr_smem(h_) <= budget_) {
+            if (rows && k3_wr_smem(h_) <= budget_) {
                 smem3w_ = k3_wr_smem(h_);
-                int nb = 0;
-                Status st = h_ == 512 ? occupancy(k3_wr<512>, NT3W, smem3w_, &nb)
-                                      : occupancy(k3_wr<256>, NT3W, smem3w_, &nb);
+                st = h_ == 512 ? occupancy(k3_wr<512>, NTr, smem3w_, &nb)
+                   : h_ == 256 ? occupancy(k3_wr<256>, NTr, smem3w_, &nb)
+                               : occupancy(k3_wr<128>, NTr, smem3w_, &nb);
                 if (!st.good()) return st;
                 if (nb >= 1) {
                     k3wr_ = true;
                     grid3w_ = std::min(B_ * ny_, nb * nsm_);
                 }
             }
-            if ((h_ == 512 || h_ == 256) && Tw1_ && k1_wr_smem(h_) <= budget_) {
+            if (rows && k1_wr_smem(h_) <= budget_) {
                 smem1w_ = k1_wr_smem(h_);
-                int nb = 0;
-                Status st = h_ == 512 ? occupancy(k1_wr<512>, NT1W, smem1w_, &nb)
-                                      : occupancy(k1_wr<256>, NT1W, smem1w_, &nb);
+                st = h_ == 512 ? occupancy(k1_wr<512>, NTr, smem1w_, &nb)
+                   : h_ == 256 ? occupancy(k1_wr<256>, NTr, smem1w_, &nb)
+                               : occupancy(k1_wr<128>, NTr, smem1w_, &nb);
                 if (!st.good()) return st;
                 if (nb >= 1) {
                     k1wr_ = true;
                     grid1w_ = std::min(B_ * ny_, nb * nsm_);
                 }
             }
-            const int TWw = ny_ == 1024 ? 8 : 16, NTw = TWw * (ny_ == 1024 ? 32 : 16);
+            const int TWw = Twc_ ? col_tw_host(ny_) : 1, NTw = TWw * (Twc_ ? col_p_host(ny_) : 1);
             if (Twc_ && h_ % TWw == 0) {
                 // one or two tile buffers: the most blocks per SM, then two
                 // (FFTLB_COLWR_NBUF fixes the count at build time)
@@ -1552,10 +1556,10 @@ class EngineT : public Engine {
 #endif
                     const size_t sm = kcol_wr_smem(ny_, h_, nb2);
                     if (sm > budget_) continue;
-                    int nb = 0;
-                    Status st = ny_ == 1024 ? occupancy(kcol_wr<1024>, NTw, sm, &nb)
-                              : ny_ == 512  ? occupancy(kcol_wr<512>, NTw, sm, &nb)
-                                            : occupancy(kcol_wr<256>, NTw, sm, &nb);
+                    st = ny_ == 1024 ? occupancy(kcol_wr<1024>, NTw, sm, &nb)
+                       : ny_ == 512  ? occupancy(kcol_wr<512>, NTw, sm, &nb)
+                       : ny_ == 256  ? occupancy(kcol_wr<256>, NTw, sm, &nb)
+                                     : occupancy(kcol_wr<128>, NTw, sm, &nb);
                     if (!st.good()) return st;
                     if (nb > best) {
                         best = nb;
@@ -1564,16 +1568,18 @@ class EngineT : public Engine {
                     }
                 }
                 if (best > 0) {
-                    Status st = make_tmap(&tmap_convw_, TWw);
+                    st = make_tmap(&tmap_convw_, TWw);
                     if (!st.good()) return st;
                     colwr_ = true;
+                    ntcw_ = NTw;
                     gridcw_ = best * nsm_;
                     const size_t sm = kcolm_wr_smem(ny_, h_);
-                    int nb = 0;
+                    nb = 0;
                     if (sm <= budget_) {
                         st = ny_ == 1024 ? occupancy(kcolm_wr<1024>, NTw, sm, &nb)
                            : ny_ == 512  ? occupancy(kcolm_wr<512>, NTw, sm, &nb)
-                                         : occupancy(kcolm_wr<256>, NTw, sm, &nb);
+                           : ny_ == 256  ? occupancy(kcolm_wr<256>, NTw, sm, &nb)
+                                         : occupancy(kcolm_wr<128>, NTw, sm, &nb);
                         if (!st.good()) return st;
                     }
                     if (nb > 0) {
@@ -1774,28 +1780,26 @@ class EngineT : public Engine {
     Status launch_col(int first, int count, bool level1) {
         if constexpr (wr_ok_) {
             if (!level1 && colwr_) {
-                if (ny_ == 1024)
-                    kcol_wr<1024><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
-                                                                       kp_, BOXR_, nbufcw_, tmap_convw_, err_);
-                else if (ny_ == 512)
-                    kcol_wr<512><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
-                                                                      kp_, BOXR_, nbufcw_, tmap_convw_, err_);
-                else
-                    kcol_wr<256><<<gridcw_, 256, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_,
-                                                                      kp_, BOXR_, nbufcw_, tmap_convw_, err_);
+#define FFTLB_KCOLWR(NYV)                                                                                     \
+    kcol_wr<NYV><<<gridcw_, ntcw_, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_, kp_, BOXR_, \
+                                                       nbufcw_, tmap_convw_, err_)
+                if (ny_ == 1024) FFTLB_KCOLWR(1024);
+                else if (ny_ == 512) FFTLB_KCOLWR(512);
+                else if (ny_ == 256) FFTLB_KCOLWR(256);
+                else FFTLB_KCOLWR(128);
+#undef FFTLB_KCOLWR
                 FFTLB_LAUNCHED("kcol_wr");
                 return Status::ok();
             }
             if (level1 && colmwr_) {
-                if (ny_ == 1024)
-                    kcolm_wr<1024><<<gridcmw_, 256, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_,
-                                                                          Twc_, kp_, BOXR_, tmap_convw_, err_);
-                else if (ny_ == 512)
-                    kcolm_wr<512><<<gridcmw_, 256, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_,
-                                                                         Twc_, kp_, BOXR_, tmap_convw_, err_);
-                else
-                    kcolm_wr<256><<<gridcmw_, 256, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_,
-                                                                         Twc_, kp_, BOXR_, tmap_convw_, err_);
+#define FFTLB_KCOLMWR(NYV)                                                                                    \
+    kcolm_wr<NYV><<<gridcmw_, ntcw_, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_, kp_,   \
+                                                          BOXR_, tmap_convw_, err_)
+                if (ny_ == 1024) FFTLB_KCOLMWR(1024);
+                else if (ny_ == 512) FFTLB_KCOLMWR(512);
+                else if (ny_ == 256) FFTLB_KCOLMWR(256);
+                else FFTLB_KCOLMWR(128);
+#undef FFTLB_KCOLMWR
                 FFTLB_LAUNCHED("kcolm_wr");
                 return Status::ok();
             }
@@ -1821,10 +1825,13 @@ class EngineT : public Engine {
         bool k1done = false;
         if constexpr (wr_ok_) {
             if (k1wr_) {
+                const int nt = nt_wr_host(h_);
                 if (h_ == 512)
-                    k1_wr<512><<<grid1w_, NT1W, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
+                    k1_wr<512><<<grid1w_, nt, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
+                else if (h_ == 256)
+                    k1_wr<256><<<grid1w_, nt, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
                 else
-                    k1_wr<256><<<grid1w_, NT1W, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
+                    k1_wr<128><<<grid1w_, nt, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
                 k1done = true;
             }
         }
@@ -1851,10 +1858,13 @@ class EngineT : public Engine {
         bool k3done = false;
         if constexpr (wr_ok_) {
             if (k3wr_) {
+                const int nt = nt_wr_host(h_);
                 if (h_ == 512)
-                    k3_wr<512><<<grid3w_, NT3W, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                    k3_wr<512><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                else if (h_ == 256)
+                    k3_wr<256><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
                 else
-                    k3_wr<256><<<grid3w_, NT3W, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                    k3_wr<128><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
                 k3done = true;
             }
         }
@@ -1871,12 +1881,16 @@ class EngineT : public Engine {
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         if constexpr (wr_ok_) {
             if (k5wr_) {
+                const int nt = nt_wr_host(h_);
                 if (h_ == 512)
-                    k5_wr<512><<<grid5w_, NT5W, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
-                                                                    beta, Tw1_, Wp_, kp_, err_);
+                    k5_wr<512><<<grid5w_, nt, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
+                                                                  beta, Tw1_, Wp_, kp_, err_);
+                else if (h_ == 256)
+                    k5_wr<256><<<grid5w_, nt, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
+                                                                  beta, Tw1_, Wp_, kp_, err_);
                 else
-                    k5_wr<256><<<grid5w_, NT5W, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
-                                                                    beta, Tw1_, Wp_, kp_, err_);
+                    k5_wr<128><<<grid5w_, nt, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
+                                                                  beta, Tw1_, Wp_, kp_, err_);
                 FFTLB_LAUNCHED("k5_wr");
                 return prof_end();
             }

@@ -77,6 +77,11 @@ template <> struct RowCfg<512> { static constexpr int E = 16, P = 32; };
 template <> struct RowCfg<256> { static constexpr int E = 16, P = 16; };
 template <> struct RowCfg<128> { static constexpr int E = 16, P = 8; };
 
+// threads per block of the row kernels: 16 warps, or 8 for H = 128 (four
+// rows per warp: 32 row groups, one per convection row)
+template <int H> __host__ __device__ constexpr int nt_wr() { return H >= 256 ? 512 : 256; }
+inline int nt_wr_host(int H) { return H >= 256 ? 512 : 256; }
+
 // position of stage-1 output (l, k1) in the row buffer.  P >= 16: k1 P +
 // (l ^ (k1 mod P)) (for P = 2E, k1 < E: k1 P + (l ^ k1)); P = 8: the row
 // parity rsw also flips bit 0 of k1, so that the two rows of a half-warp use
@@ -234,15 +239,13 @@ __device__ __forceinline__ void c2r_pre_wr(C *z, const C *Wp, int j) {
 // pass (one per row group), two chunk buffers.
 // ---------------------------------------------------------------------------
 
-constexpr int NT1W = 512;
-
 template <int H>
-__global__ void __launch_bounds__(NT1W, 1) k1_wr(const float *__restrict__ f, float2 *spec, float *__restrict__ fields,
+__global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const float *__restrict__ f, float2 *spec, float *__restrict__ fields,
                                                  const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
                                                  KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = NT1W, NWARP = NT / 32;
+    constexpr int NX = 2 * H, NT = nt_wr<H>(), NWARP = NT / 32;
     constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
     constexpr int NG = NWARP * RPW;                // row groups per block
     constexpr int CH = NG + 1, NCH = NMOV / NG;    // rows per chunk buffer, chunks per row
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(NT1W, 1) k1_wr(const float *__restrict__ f, fl
 // shared memory of k1_wr<H>
 inline size_t k1_wr_smem(int H) {
     const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
-    const int CH = (NT1W / 32) * (32 / P) + 1;
+    const int CH = (nt_wr_host(H) / 32) * (32 / P) + 1;
     return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4,
                        (size_t)6 * 2 * H * 4});
 }
@@ -382,8 +385,6 @@ inline size_t k1_wr_smem(int H) {
 // transforms.  Persistent over the rows of all runs, one row per pass, two
 // buffers (15 spectrum rows + rho, T), the next-but-one row prefetched.
 // ---------------------------------------------------------------------------
-
-constexpr int NT3W = 512;
 
 template <typename real>
 __device__ __forceinline__ void k3_issue(const typename cplx_of<real>::type *spec, const real *fields, real *dst,
@@ -401,12 +402,12 @@ __device__ __forceinline__ void k3_issue(const typename cplx_of<real>::type *spe
 }
 
 template <int H>
-__global__ void __launch_bounds__(NT3W, 1) k3_wr(float2 *spec, const float *__restrict__ fields,
+__global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *spec, const float *__restrict__ fields,
                                                  float *__restrict__ aux, const float2 *__restrict__ tw_g,
                                                  const float2 *__restrict__ Wp_g, KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = NT3W, NWARP = NT / 32;
+    constexpr int NX = 2 * H, NT = nt_wr<H>(), NWARP = NT / 32;
     constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
     constexpr int SMAX = (NX + NT - 1) / NT;
     constexpr int RB = ND1 + 2;   // rows per buffer
@@ -531,17 +532,15 @@ inline size_t k3_wr_smem(int H) {
 // H = 512, all four for H = 256).
 // ---------------------------------------------------------------------------
 
-constexpr int NT5W = 512;
-
 template <int H>
-__global__ void __launch_bounds__(NT5W, 1) k5_wr(const float2 *spec, const float *__restrict__ fields,
+__global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k5_wr(const float2 *spec, const float *__restrict__ fields,
                                                  const float *__restrict__ aux, const float *fcur, const float *fbase,
                                                  float *fout, float alpha, float beta,
                                                  const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
                                                  KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = NT5W, NWARP = NT / 32;
+    constexpr int NX = 2 * H, NT = nt_wr<H>(), NWARP = NT / 32;
     constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;          // lanes per row, rows per warp
     constexpr int CH = NWARP * RPW, NCH = NMOV / CH;           // rows per chunk, chunks per row
     constexpr int NRING = CH / 8;                              // rings per chunk
@@ -777,6 +776,9 @@ template <int NY> struct ColCfg;
 template <> struct ColCfg<1024> { static constexpr int E = 32, P = 32, TW = 8; };
 template <> struct ColCfg<512> { static constexpr int E = 32, P = 16, TW = 16; };
 template <> struct ColCfg<256> { static constexpr int E = 16, P = 16, TW = 16; };
+template <> struct ColCfg<128> { static constexpr int E = 16, P = 8, TW = 32; };
+inline int col_tw_host(int NY) { return NY == 1024 ? 8 : NY == 128 ? 32 : 16; }
+inline int col_p_host(int NY) { return NY == 1024 ? 32 : NY == 128 ? 8 : 16; }
 
 template <int NY>
 __device__ __forceinline__ int cpos(int c, int l, int k1) {
@@ -1052,14 +1054,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
 
 // shared memory of kcolm_wr<NY>
 inline size_t kcolm_wr_smem(int NY, int h) {
-    const int TW = NY == 1024 ? 8 : 16;
+    const int TW = col_tw_host(NY);
     const size_t tile = (size_t)TW * NY * 8;
     return smem_bytes({(size_t)2 * NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, 2 * tile, tile});
 }
 
 // shared memory of kcol_wr<NY> with nbuf tile buffers
 inline size_t kcol_wr_smem(int NY, int h, int nbuf) {
-    const int TW = NY == 1024 ? 8 : 16;
+    const int TW = col_tw_host(NY);
     const size_t tile = (size_t)TW * NY * 8;
     return smem_bytes({(size_t)2 * NY * 8, (size_t)(h + 1) * 4, (size_t)NY * 4, tile, nbuf > 1 ? tile : 0});
 }
@@ -1067,7 +1069,7 @@ inline size_t kcol_wr_smem(int NY, int h, int nbuf) {
 // shared memory of k5_wr<H>
 inline size_t k5_wr_smem(int H) {
     const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
-    const int CH = (NT5W / 32) * (32 / P);
+    const int CH = (nt_wr_host(H) / 32) * (32 / P);
     return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)NHEAD * 2 * H * 4, (size_t)NHEAD * 2 * H * 4,
                        (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4});
 }

@@ -29,6 +29,55 @@ def _rank_main(rank, world, port, out):
     rep.close()
 
 
+def _sweep_rank_main(rank, world, port, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1011_3582_gb300 import workloads
+    rep = bench.Replicas("gloo", "cpu")
+    plan = workloads.sweep_plan(64, seed=3)
+    mine = bench.sweep_shard(plan, rep.rank, rep.world)
+    local = [(idx, {"n": n, "tr": tr, "rank": rank}) for idx, (n, tr) in mine]
+    out[rank] = (rep.gather(local), len(mine))
+    rep.close()
+
+
+def test_sweep_runs_partitioned_across_two_ranks_and_gathered():
+    """The sweep's natural shard: rank r takes runs r, r + N, ... of the plan
+    (no data-path collective); every rank's per-run results reach every
+    rank, and together they cover each of the 64 runs exactly once, with
+    the run's own grid and temperature."""
+    sys.path.insert(0, ROOT)
+    from paper_1011_3582_gb300 import workloads
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    mp.start_processes(_sweep_rank_main, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+    plan = workloads.sweep_plan(64, seed=3)
+    gathered, sizes = out[0][0], [out[r][1] for r in range(world)]
+    assert sizes == [32, 32]
+    flat = [x for part in gathered for x in part]
+    assert sorted(i for i, _ in flat) == list(range(64))
+    for i, res in flat:
+        assert (res["n"], res["tr"]) == plan[i] and res["rank"] == i % world
+    assert out[1][0] == gathered
+
+
+def test_sweep_slab_densities_table():
+    """bench.py lays out the sweep's slabs from tests/golden/maxwell_9_49.json
+    by linear interpolation: within 1e-5 of the oracle's Maxwell densities
+    between the table's grid points."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import thermo as TH
+    table = bench.maxwell_table()
+    a, b = 9 / 49, 2 / 21
+    for tr in (0.7, 0.7437, 0.85, 0.9123, 0.99):
+        rv, rl = bench.coexistence_densities(table, tr)
+        wv, wl = TH.maxwell(tr * 8 * a / (27 * b), a, b)
+        assert abs(rv - wv) / wv < 1e-5 and abs(rl - wl) / wl < 1e-5
+
+
 def test_two_ranks_max_time_and_whole_job_throughput():
     world, port = 2, _free_port()
     ctx = mp.get_context("spawn")

@@ -381,10 +381,10 @@ def test_droplet_512_precision_config(fl, precision):
 
 
 @pytest.mark.parametrize("nx,ny", [(1024, 32), (512, 48), (512, 16), (1024, 96), (16, 1024), (32, 512), (64, 256),
-                                   (48, 1024), (96, 512)])
+                                   (48, 1024), (96, 512), (256, 16), (256, 48), (16, 128), (48, 128)])
 def test_wide_rows_fp32(fl, nx, ny):
-    """Row widths nx = 512 and 1024 and column lengths ny = 256, 512 and
-    1024, where the fp32 path runs its warp-resident row and column
+    """Row widths nx = 256, 512 and 1024 and column lengths ny = 128, 256,
+    512 and 1024, where the fp32 path runs its warp-resident row and column
     kernels, on narrow grids (the other axis 16 to 96, the radix-3 lengths
     48 and 96 included) against the oracle after 3 SSP-RK3 steps of a
     spinodal quench at T = 0.8 T_c, element by element within

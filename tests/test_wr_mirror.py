@@ -53,7 +53,7 @@ def test_real_rows_round_trip(H):
     assert np.allclose(y, 2 * H * x)
 
 
-@pytest.mark.parametrize("NY", [1024, 512, 256])
+@pytest.mark.parametrize("NY", [1024, 512, 256, 128])
 def test_column_tile_transform(NY):
     """kcol_wr's index arithmetic: forward, multiplier, inverse equals
     NY * IDFT(m DFT(x)) per column of the tile."""
@@ -66,7 +66,7 @@ def test_column_tile_transform(NY):
     assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("NY", [1024, 512, 256])
+@pytest.mark.parametrize("NY", [1024, 512, 256, 128])
 def test_column_tile_layout(NY):
     """The swizzled positions are a permutation of the tile; the rows a
     thread's in-place store overwrites were read by threads of its own warp

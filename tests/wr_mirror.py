@@ -146,7 +146,7 @@ def c2r_pre(X, H):
     return z
 
 
-COLCFG = {1024: (32, 32, 8), 512: (32, 16, 16), 256: (16, 16, 16)}   # NY: (E, P, TW)
+COLCFG = {1024: (32, 32, 8), 512: (32, 16, 16), 256: (16, 16, 16), 128: (16, 8, 32)}   # NY: (E, P, TW)
 
 
 def cpos(NY, c, l, k1):
