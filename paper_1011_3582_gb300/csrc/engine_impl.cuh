@@ -1513,7 +1513,7 @@ class EngineT : public Engine {
             Status st;
             if (rows && k5_wr_smem(h_) <= budget_) {
                 smem5w_ = k5_wr_smem(h_);
-                st = h_ == 512 ? occupancy(k5_wr<512>, NTr, smem5w_, &nb)
+                st = h_ == 512 ? occupancy(k5_wr<512>, nt_k5wr_host(h_), smem5w_, &nb)
                    : h_ == 256 ? occupancy(k5_wr<256>, NTr, smem5w_, &nb)
                                : occupancy(k5_wr<128>, NTr, smem5w_, &nb);
                 if (!st.good()) return st;
@@ -1881,7 +1881,7 @@ class EngineT : public Engine {
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         if constexpr (wr_ok_) {
             if (k5wr_) {
-                const int nt = nt_wr_host(h_);
+                const int nt = nt_k5wr_host(h_);
                 if (h_ == 512)
                     k5_wr<512><<<grid5w_, nt, smem5w_, stream_>>>(specb_, fieldsb_, auxb_, cur, base, out, alpha,
                                                                   beta, Tw1_, Wp_, kp_, err_);

@@ -79,8 +79,20 @@ template <> struct RowCfg<128> { static constexpr int E = 16, P = 8; };
 
 // threads per block of the row kernels: 16 warps, or 8 for H = 128 (four
 // rows per warp: 32 row groups, one per convection row)
+// Threads of the final row kernel at H = 512: 256, i.e. two blocks per SM,
+// each with one head buffer and one-ring chunks (measured at 1024^2: 131 us
+// against 146 us for one 512-thread block with two head buffers; the
+// FFTLB_K5_NT512 build flag selects 512)
+#ifndef FFTLB_K5_NT512
+#define FFTLB_K5_NT512 256
+#endif
 template <int H> __host__ __device__ constexpr int nt_wr() { return H >= 256 ? 512 : 256; }
 inline int nt_wr_host(int H) { return H >= 256 ? 512 : 256; }
+template <int H> __host__ __device__ constexpr int nt_k5wr() { return H == 512 ? FFTLB_K5_NT512 : nt_wr<H>(); }
+inline int nt_k5wr_host(int H) { return H == 512 ? FFTLB_K5_NT512 : nt_wr_host(H); }
+// head buffers of the final row kernel: two (the next row's head fetched a
+// row ahead) unless its blocks are half size
+template <int H> __host__ __device__ constexpr int nhb_k5wr() { return nt_k5wr<H>() == 512 || H < 256 ? 2 : 1; }
 
 // position of stage-1 output (l, k1) in the row buffer.  P >= 16: k1 P +
 // (l ^ (k1 mod P)) (for P = 2E, k1 < E: k1 P + (l ^ k1)); P = 8: the row
@@ -533,14 +545,14 @@ inline size_t k3_wr_smem(int H) {
 // ---------------------------------------------------------------------------
 
 template <int H>
-__global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k5_wr(const float2 *spec, const float *__restrict__ fields,
+__global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_wr(const float2 *spec, const float *__restrict__ fields,
                                                  const float *__restrict__ aux, const float *fcur, const float *fbase,
                                                  float *fout, float alpha, float beta,
                                                  const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
                                                  KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = nt_wr<H>(), NWARP = NT / 32;
+    constexpr int NX = 2 * H, NT = nt_k5wr<H>(), NWARP = NT / 32, NHB = nhb_k5wr<H>();
     constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;          // lanes per row, rows per warp
     constexpr int CH = NWARP * RPW, NCH = NMOV / CH;           // rows per chunk, chunks per row
     constexpr int NRING = CH / 8;                              // rings per chunk
@@ -556,7 +568,7 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k5_wr(const floa
     C *tw = (C *)sc.take(H * sizeof(C));
     C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
     real *head0 = (real *)sc.take((size_t)NHEAD * NX * sizeof(real));
-    real *head1 = (real *)sc.take((size_t)NHEAD * NX * sizeof(real));
+    real *head1 = NHB > 1 ? (real *)sc.take((size_t)NHEAD * NX * sizeof(real)) : head0;
     real *buf0 = (real *)sc.take((size_t)CH * NX * sizeof(real));
     real *buf1 = (real *)sc.take((size_t)CH * NX * sizeof(real));
     const int NY = P.nrun * ny;
@@ -574,18 +586,18 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k5_wr(const floa
     __syncthreads();
     if (tid == 0) {
         if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, H);
-        if (nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, H);
+        if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, H);
         if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, NCH, CH, nx, ny, slot, H);
         if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, NCH, CH, nx, ny, slot, H);
     }
     uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
-    bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = nrows > 1;
+    bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
     const real dt = P.dt, itau = real(1) / P.tau;
     const bool with_base = alpha != real(0);
     for (int jb = 0; jb < njobs; ++jb) {
         const bool odd = jb & 1;
         const int ri = jb / NCH, c = jb - ri * NCH;
-        const bool hodd = ri & 1;
+        const bool hodd = NHB > 1 && (ri & 1);
         const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
         const int run = yg / ny, y = yg - run * ny;
         const size_t fo = (size_t)run * Q * N;
@@ -741,8 +753,8 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k5_wr(const floa
                 if (nodd) pend1 = true;
                 else pend0 = true;
             }
-            if (c == NCH - 1 && ri + 2 < nrows) {
-                k5_issue_head<real>(spec, fields, aux, Hd, hodd ? &hbar1 : &hbar0, ri + 2, nx, ny, N, slot, H);
+            if (c == NCH - 1 && ri + NHB < nrows) {   // the row's head buffer is free
+                k5_issue_head<real>(spec, fields, aux, Hd, hodd ? &hbar1 : &hbar0, ri + NHB, nx, ny, N, slot, H);
                 if (hodd) hpend1 = true;
                 else hpend0 = true;
             }
@@ -772,12 +784,18 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k5_wr(const floa
 // the multiplier at k_x = 0, because the Nyquist bin of k_x is zero.
 // ---------------------------------------------------------------------------
 
+// (FFTLB_COL1024_TW: the 1024-point tile width, 8 by default; 4 halves the
+// blocks and doubles their number per SM, measured slower: convection 102 ->
+// 112 us, level 1 62 -> 96 us at 1024^2)
+#ifndef FFTLB_COL1024_TW
+#define FFTLB_COL1024_TW 8
+#endif
 template <int NY> struct ColCfg;
-template <> struct ColCfg<1024> { static constexpr int E = 32, P = 32, TW = 8; };
+template <> struct ColCfg<1024> { static constexpr int E = 32, P = 32, TW = FFTLB_COL1024_TW; };
 template <> struct ColCfg<512> { static constexpr int E = 32, P = 16, TW = 16; };
 template <> struct ColCfg<256> { static constexpr int E = 16, P = 16, TW = 16; };
 template <> struct ColCfg<128> { static constexpr int E = 16, P = 8, TW = 32; };
-inline int col_tw_host(int NY) { return NY == 1024 ? 8 : NY == 128 ? 32 : 16; }
+inline int col_tw_host(int NY) { return NY == 1024 ? FFTLB_COL1024_TW : NY == 128 ? 32 : 16; }
 inline int col_p_host(int NY) { return NY == 1024 ? 32 : NY == 128 ? 8 : 16; }
 
 template <int NY>
@@ -787,7 +805,7 @@ __device__ __forceinline__ int cpos(int c, int l, int k1) {
 }
 
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 2) kcol_wr(float2 *spec,
+__global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW * ColCfg<NY>::P >= 256 ? 2 : 4) kcol_wr(float2 *spec,
                                                                              const GroupDesc *__restrict__ groups,
                                                                              int ngroups,
                                                                              const float *__restrict__ kxt,
@@ -1069,9 +1087,10 @@ inline size_t kcol_wr_smem(int NY, int h, int nbuf) {
 // shared memory of k5_wr<H>
 inline size_t k5_wr_smem(int H) {
     const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
-    const int CH = (nt_wr_host(H) / 32) * (32 / P);
-    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)NHEAD * 2 * H * 4, (size_t)NHEAD * 2 * H * 4,
-                       (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4});
+    const int NT = nt_k5wr_host(H), CH = (NT / 32) * (32 / P);
+    const int NHB = NT == 512 || H < 256 ? 2 : 1;
+    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)NHEAD * 2 * H * 4,
+                       NHB > 1 ? (size_t)NHEAD * 2 * H * 4 : 0, (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4});
 }
 
 }  // namespace fftlb
