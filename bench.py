@@ -120,13 +120,15 @@ def write_ncu_traffic(csv_path, precision, n, note, out_path=None):
     out, multi = {}, 0
     for i in sorted(per):
         name, by = per[i]
-        if "k1_pipe" in name:
+        if "k1_pipe" in name or "k1_wr" in name:
             k = "row_forward_moments"
-        elif "k3_pipe" in name:
+        elif "k3_pipe" in name or "k3_wr" in name:
             k = "row_level1"
-        elif "k5_pipe" in name:
+        elif "k5_pipe" in name or "k5_wr" in name:
             k = "row_final"
-        elif "kcol_pipe" in name:
+        elif "kcol_wr" in name:
+            k = "col_convection"
+        elif "kcol_pipe" in name or "kcolm_wr" in name:
             m = re.search(r"kcol_pipe<\s*\w+\s*,\s*(\w+)", name)   # the second template argument: MULTI
             if m and m.group(1) in ("false", "0"):
                 k = "col_convection"
