@@ -191,3 +191,57 @@ def test_laplace_fp64(fl):
     print("a9/49 fp64 t=4: R_e %s dP %s sigma %.4e theory %.4e" % (x["R_e"], x["dP"], x["sigma_fit"], x["sigma_theory"]))
     _dump("laplace_fp64", x)
     assert x["finite"]
+
+
+@LONG
+def test_triangle_spurious_velocity(fl):
+    """The relaxation of a triangular drop (Sec. 4.2, Figs. 17-19): an
+    equilateral triangle of side 64 with a sharp edge in a 128^2 box,
+    (rho, T) = (1.46, 0.95) inside and (0.58, 0.95) outside, the paper's
+    fluid, K = 1e-5; the maximum speed u^s_max(t) with the windows k1..k4
+    in fp32 and with k4 in fp64 as well, dt = 1e-4 to t = 5 (the paper runs
+    to t = 30 at dt = 1e-5, where u^s_max has levelled off for t > 20).
+    The paper finds u^s_max lower for every higher window order."""
+    R_eq = float(np.sqrt(np.sqrt(3.0) / 4.0 * 64 ** 2 / np.pi))   # the disc of the triangle's area
+    fields = W.triangle(128, 128, 64, 1.46, 0.58, 0.95)
+    runs = [PH.Run(fl.params(nx=128, ny=128, a=9 / 8, b=1 / 3, K=1e-5, dt=1e-4, precision=prec, integrator=3,
+                             window=w), fields, "droplet", R=R_eq)
+            for prec, w in ((32, 1), (32, 2), (32, 3), (32, 4), (64, 4))]
+    res = PH.relax(fl, runs, t_end=5.0, sample_dt=0.05, avg_from=0.8)
+    curves = {}
+    for (prec, w), r in zip(((32, 1), (32, 2), (32, 3), (32, 4), (64, 4)), res):
+        t = [s[0] for s in r["samples"]]
+        um = [s[1]["umax"] for s in r["samples"]]
+        curves["fp%d_k%d" % (prec, w)] = dict(t=t, umax=um, finite=r["finite"])
+        print("fp%d k%d: u^s_max at t = 0.5, 1, 2, 3, 5: %s" % (prec, w, ["%.3e" % um[int(round(x / 0.05)) - 1]
+                                                                         for x in (0.5, 1, 2, 3, 5)]))
+    u32, u64 = np.array(curves["fp32_k4"]["umax"]), np.array(curves["fp64_k4"]["umax"])
+    print("fp32 vs fp64 (k4): largest relative difference of u^s_max over t in [1, 5]: %.2e"
+          % (np.abs(u32 - u64)[19:] / u64[19:]).max())
+    _dump("triangle", curves)
+    assert all(c["finite"] for c in curves.values())
+
+
+@LONG
+def test_energy_drift_by_window(fl):
+    """Total-energy variation Delta e_T(t) = e_T(t) - e_T(0) of the phase
+    separation of Fig. 2 / Fig. 8 (128^2, rho = 1 + U(-1e-3, 1e-3), T = 0.85,
+    the paper's fluid, K = 1e-5) with the windows k1..k4 in fp64, and k4 in
+    fp32, dt = 1e-4 to t = 2.  The paper finds |Delta e_T| smaller for every
+    higher window order."""
+    fields = W.slab(128, 128, 1.0, 1.0, 0.85, noise=1e-3, seed=8)
+    runs = [PH.Run(fl.params(nx=128, ny=128, a=9 / 8, b=1 / 3, K=1e-5, dt=1e-4, precision=prec, integrator=3,
+                             window=w), fields, "slab", "y")
+            for prec, w in ((64, 1), (64, 2), (64, 3), (64, 4), (32, 4))]
+    res = PH.relax(fl, runs, t_end=2.0, sample_dt=0.02)
+    curves = {}
+    for (prec, w), r in zip(((64, 1), (64, 2), (64, 3), (64, 4), (32, 4)), res):
+        t = [s[0] for s in r["samples"]]
+        e = np.array([s[2]["eT"] for s in r["samples"]])
+        m = np.array([s[2]["mass"] for s in r["samples"]])
+        curves["fp%d_k%d" % (prec, w)] = dict(t=t, dEt=(e - e[0]).tolist(), eT0=float(e[0]),
+                                               mass_drift=float(np.abs(m - m[0]).max() / m[0]), finite=r["finite"])
+        print("fp%d k%d: e_T(0) = %.6f, max |Delta e_T| = %.3e, |Delta e_T(2)| = %.3e, mass drift %.1e"
+              % (prec, w, e[0], np.abs(e - e[0]).max(), abs(e[-1] - e[0]), curves["fp%d_k%d" % (prec, w)]["mass_drift"]))
+    _dump("energy_drift", curves)
+    assert all(c["finite"] for c in curves.values())
