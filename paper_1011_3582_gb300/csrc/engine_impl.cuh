@@ -11,13 +11,18 @@
 //                           moving f_i and of rho, u_x, u_y, T, Pi, g
 //   kcol_pipe (col_convection)  column forward -> i (v_x k_m,x + v_y k_m,y)
 //                           -> column inverse for the 32 f_i (in place)
-//   kcol_pipe (col_level1)  15 derivative spectra of rho, u, T, Pi, g
-//   k3_pipe (row_level1)    row inverse of the 15 derivatives; Lambda
-//                           (Eq. 19), Phi = 2 q rho T grad T (Eq. 23), the
-//                           numerators of C (Eq. 22) and B (Eq. 21); forward
-//                           row transforms of Lambda_xx, Lambda_xy,
-//                           Lambda_yy, Phi_x, Phi_y
-//   kcol_pipe (col_level2)  d_b Lambda_xb, d_b Lambda_yb, d_a Phi_a
+//   kcol_pipe (col_level1)  the 8 level-1 derivative spectra that involve
+//                           k_y (d_y of rho, u, T, Pi, g; d_yy rho;
+//                           d_y div u)
+//   k3_pipe (row_level1)    the 7 derivatives in k_x alone, formed in the
+//                           row spectrum (k3_form_x); row inverse of the
+//                           15; Lambda (Eq. 19), Phi = 2 q rho T grad T
+//                           (Eq. 23), the numerators of C (Eq. 22) and B
+//                           (Eq. 21); forward row transforms of Lambda_xx,
+//                           Lambda_xy, Lambda_yy, Phi_x, Phi_y, with the
+//                           d_x terms of level 2 formed in the row spectrum
+//   kcol_pipe (col_level2)  d_b Lambda_xb, d_b Lambda_yb, d_a Phi_a: the
+//                           column pass of the d_y terms plus the d_x terms
 //   k5_pipe (row_final)     row inverse of the convection terms and level-2
 //                           divergences; A, B, C, C_q (Eqs. 20-23), f^eq
 //                           (Eq. 3), I (Eq. 11), BGK and the RK combination.
@@ -57,6 +62,36 @@ constexpr int ND1 = 15;
 constexpr int SLOT_L2 = 53;      // Lxx, Lxy, Lyy, Phx, Phy; outputs in 53, 55, 56
 constexpr int NSLOT = 58;
 enum { D_RX, D_RY, D_LAP, D_UXX, D_UXY, D_UYX, D_UYY, D_DIVX, D_DIVY, D_TX, D_TY, D_PIX, D_PIY, D_GX, D_GY };
+
+// The windowed derivative multipliers are separable: D_x = i k_x (a
+// function of k_x alone), D_y = i k_y, and the second derivatives are their
+// products (Eqs. K1-K4 with the real part taken after each derivative, so
+// that the Nyquist bins carry zero).  A derivative whose multiplier depends
+// on k_x alone needs no column transform: in the row-transformed slot it is
+// the pointwise product i k_x X / nx (the 1 / nx that the column pass would
+// leave).  So the level-1 column pass forms only the outputs that involve
+// k_y, 8 of the 15 (d_y of rho, u_x, u_y, T, Pi, g; d_yy rho;
+// d_xy u_x + d_yy u_y), and the row kernel K3 forms the other 7 from the
+// row spectra of rho, u_x, u_y, T, Pi, g before its inverse rows:
+//   rho_x = i k_x rho^ / nx, lap rho = d_yy rho - k_x^2 rho^ / nx,
+//   u_xx = i k_x u_x^ / nx, u_yx = i k_x u_y^ / nx,
+//   d_x(div u) = i k_x (u_xx + u_yy), T_x, Pi_x, g_x = i k_x (.)^ / nx.
+// Level 2 in the same way: d_x Lambda_xx + d_y Lambda_xy is the column
+// pass of d_y Lambda_xy plus i k_x Lambda_xx^ / nx, formed by K3 (add_slot).
+// k3_src_slot(o): the slot K3 loads into its row o (-1: formed in K3).
+__host__ __device__ constexpr int k3_src_slot(int o) {
+    return o == D_RX ? SLOT_RHO : o == D_UXX ? SLOT_UX : o == D_UYX ? SLOT_UY : o == D_TX ? SLOT_T
+         : o == D_PIX ? SLOT_PI : o == D_GX ? SLOT_G : o == D_DIVX ? -1 : SLOT_D1 + o;
+}
+// K3's level-2 outputs: row r of Lambda_xx, Lambda_xy, Lambda_yy, Phi_x,
+// Phi_y goes to slot k3_raw_slot(r) as it is and to slot k3_mul_slot(r)
+// times i k_x / nx (-1: not written)
+__host__ __device__ constexpr int k3_raw_slot(int r) {
+    return r == 1 ? SLOT_L2 + 1 : r == 2 ? SLOT_L2 + 2 : r == 4 ? SLOT_L2 + 4 : -1;
+}
+__host__ __device__ constexpr int k3_mul_slot(int r) {
+    return r == 0 ? SLOT_L2 + 0 : r == 1 ? SLOT_D1 + D_DIVX : r == 3 ? SLOT_L2 + 3 : -1;
+}
 
 // velocity set (Eq. 1) and weight-polynomial coefficients (Eq. 4); each
 // translation unit holds its own copy, shared by all live engines of that
@@ -98,12 +133,17 @@ template <> __device__ __forceinline__ float FKC<float>(int k, int j) { return c
 template <typename real> struct KP {
     int nx, ny, h, nrun;
     real dx, dt, tau, a, b, K, H, q, zeta, scale;
+    real scale_x;   // 1 / nx: the inverse normalisation a column pass leaves to the rows (scale * ny)
     const uint4 *tc16;
 };
 
 // One column-pass group: up to 2 input spectra and 6 outputs; every output
 // is a sum of up to 2 terms M(kx, ky) * input, with
 // M = i (c0 k_x + c1 k_y) + (c2 k_x^2 + c3 k_y^2 + c4 k_x k_y).
+// add_slot >= 0 (groups of one input and one output, the convection kernels
+// only): the column inverse of that output is added to slot add_slot's
+// values at the same positions (a term that needs no column transform,
+// formed by the row kernel that wrote add_slot).
 struct GroupDesc {
     int nin, nout;
     int in_slot[2];
@@ -111,6 +151,7 @@ struct GroupDesc {
     int nterm[6];
     int term_in[6][2];
     double c[6][2][5];
+    int add_slot;
 };
 
 // ---------------------------------------------------------------------------
@@ -817,9 +858,9 @@ class EngineT : public Engine {
         const double alg[KK_COUNT] = {
             (33 + 38 + 4) * NN * s,                   // f in; 38 spectra + rho, u, T out
             (32 + 32) * NN * s,                       // 32 spectra in, 32 out
-            (6 + 15) * NN * s,                        // 6 in, 15 out
-            (15 + 2 + 3 + 5) * NN * s,                // 15 + rho, T in; 3 aux + 5 spectra out
-            (5 + 3) * NN * s,                         // 5 in, 3 out
+            (6 + 8) * NN * s,                         // 6 in, 8 out
+            (14 + 2 + 3 + 6) * NN * s,                // 14 + rho, T in; 3 aux + 6 spectra out
+            (3 + 3 + 3) * NN * s,                     // 3 in, 3 added, 3 out
             (32 + 3 + 4 + 3 + 33 + 33 * fbase + 33) * NN * s};
         for (int k = 0; k < nkinds && k < KK_COUNT; ++k) {
             if (ms) ms[k] = prof_ms_[k];
@@ -1127,6 +1168,7 @@ class EngineT : public Engine {
         g.nin = nin;
         g.in_slot[0] = in0;
         g.in_slot[1] = in1;
+        g.add_slot = -1;
         return g;
     }
     // add output: term list of (input index, c0..c4)
@@ -1145,8 +1187,7 @@ class EngineT : public Engine {
 
     Status build_groups() {
         static const double DX[5] = {1, 0, 0, 0, 0}, DY[5] = {0, 1, 0, 0, 0};
-        static const double DXX[5] = {0, 0, -1, 0, 0}, DYY[5] = {0, 0, 0, -1, 0}, DXY[5] = {0, 0, 0, 0, -1};
-        static const double LAP[5] = {0, 0, -1, -1, 0};
+        static const double DYY[5] = {0, 0, 0, -1, 0}, DXY[5] = {0, 0, 0, 0, -1};
         std::vector<GroupDesc> gs;
         // convection: i (v_x k_x + v_y k_y) f_i, in place
         conv_groups_ = (int)gs.size();
@@ -1156,48 +1197,40 @@ class EngineT : public Engine {
             add_out(g, i - 1, 1, 0, c);
             gs.push_back(g);
         }
-        // level 1
+        // level 1: the outputs that involve k_y (k3_src_slot: K3 forms the rest)
         l1_groups_ = (int)gs.size();
         {
             GroupDesc g = group(1, SLOT_RHO, 0);
-            add_out(g, SLOT_D1 + D_RX, 1, 0, DX);
             add_out(g, SLOT_D1 + D_RY, 1, 0, DY);
-            add_out(g, SLOT_D1 + D_LAP, 1, 0, LAP);
+            add_out(g, SLOT_D1 + D_LAP, 1, 0, DYY);   // K3 adds -k_x^2 rho^ / nx
             gs.push_back(g);
         }
         {
             GroupDesc g = group(2, SLOT_UX, SLOT_UY);
-            add_out(g, SLOT_D1 + D_UXX, 1, 0, DX);
             add_out(g, SLOT_D1 + D_UXY, 1, 0, DY);
-            add_out(g, SLOT_D1 + D_UYX, 1, 1, DX);
             add_out(g, SLOT_D1 + D_UYY, 1, 1, DY);
-            add_out(g, SLOT_D1 + D_DIVX, 2, 0, DXX, 1, DXY);   // D_x (D_x u_x + D_y u_y)
             add_out(g, SLOT_D1 + D_DIVY, 2, 0, DXY, 1, DYY);   // D_y (D_x u_x + D_y u_y)
             gs.push_back(g);
         }
-        const int singles[3][3] = {{SLOT_T, D_TX, D_TY}, {SLOT_PI, D_PIX, D_PIY}, {SLOT_G, D_GX, D_GY}};
+        const int singles[3][2] = {{SLOT_T, D_TY}, {SLOT_PI, D_PIY}, {SLOT_G, D_GY}};
         for (auto &sgl : singles) {
             GroupDesc g = group(1, sgl[0], 0);
-            add_out(g, SLOT_D1 + sgl[1], 1, 0, DX);
-            add_out(g, SLOT_D1 + sgl[2], 1, 0, DY);
+            add_out(g, SLOT_D1 + sgl[1], 1, 0, DY);
             gs.push_back(g);
         }
-        // level 2 (outputs in place: 53, 55, 56)
+        // level 2: d_y of Lambda_xy, Lambda_yy, Phi_y plus the d_x terms K3
+        // wrote (k3_mul_slot): outputs in 53, 55, 56
         l2_groups_ = (int)gs.size();
         {
-            GroupDesc g = group(2, SLOT_L2 + 0, SLOT_L2 + 1);
-            add_out(g, SLOT_L2 + 0, 2, 0, DX, 1, DY);
-            gs.push_back(g);
-        }
-        {
-            GroupDesc g = group(2, SLOT_L2 + 1, SLOT_L2 + 2);
-            add_out(g, SLOT_L2 + 2, 2, 0, DX, 1, DY);
-            gs.push_back(g);
-        }
-        {
-            GroupDesc g = group(2, SLOT_L2 + 3, SLOT_L2 + 4);
-            add_out(g, SLOT_L2 + 3, 2, 0, DX, 1, DY);
-            gs.push_back(g);
+            const int l2[3][3] = {{SLOT_L2 + 1, SLOT_L2 + 0, SLOT_L2 + 0},          // in, out, add
+                                  {SLOT_L2 + 2, SLOT_L2 + 2, SLOT_D1 + D_DIVX},
+                                  {SLOT_L2 + 4, SLOT_L2 + 3, SLOT_L2 + 3}};
+            for (auto &e : l2) {
+                GroupDesc g = group(1, e[0], 0);
+                add_out(g, e[1], 1, 0, DY);
+                g.add_slot = e[2];
+                gs.push_back(g);
+            }
         }
         // gradient op: field i in slot i -> slots 20 + 2i, 21 + 2i
         grad_groups_ = (int)gs.size();
@@ -1228,6 +1261,7 @@ class EngineT : public Engine {
         int maxsm = 0;
         FFTLB_CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         const size_t budget = (size_t)maxsm - 2048;   // static shared memory headroom
+        optin_ = (size_t)maxsm;
         // column tile width: largest of 8, 4, 2, 1 dividing h with the
         // batched column FFT fitting the registers (TW ny <= 16 NT) and
         // 3 tiles in shared memory
@@ -1260,6 +1294,7 @@ class EngineT : public Engine {
         kp_.q = (real)p_.q;
         kp_.zeta = (real)p_.zeta;
         kp_.scale = (real)(1.0 / ((double)nx_ * (double)ny_));
+        kp_.scale_x = (real)(1.0 / (double)nx_);
         kp_.tc16 = split_ ? tc16_ : nullptr;
         return configure_pipe(budget);
     }
@@ -1297,13 +1332,20 @@ class EngineT : public Engine {
     // (the shared-memory opt-in is a per-function, process-wide attribute:
     // always the full budget, so that handles of different grids never
     // lower it below one another's needs)
+    // (the budget leaves 2 KB for static shared memory; a kernel with more
+    // gets the opt-in maximum less its own static part)
     template <typename K> Status occupancy(K kernel, int nthreads, size_t smem, int *blocks) {
-        FFTLB_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
+        cudaFuncAttributes fa;
+        FFTLB_CU(cudaFuncGetAttributes(&fa, kernel));
+        const size_t lim = std::min(budget_, optin_ > fa.sharedSizeBytes ? optin_ - fa.sharedSizeBytes : (size_t)0);
+        *blocks = 0;
+        if (smem > lim) return Status::ok();
+        FFTLB_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
         FFTLB_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, nthreads, smem));
         return Status::ok();
     }
 
-    size_t budget_ = 0;
+    size_t budget_ = 0, optin_ = 0;
     static constexpr int NT1 = KCfg<real, KS_K1>::NT, NTC = KCfg<real, KS_COL>::NT, NT5 = KCfg<real, KS_K5>::NT;
     int ntrmax() const { return std::max(ntr_, ntr8_); }
     // shared memory of the column kernel: twiddles, pass tables, k tables,
@@ -1780,6 +1822,7 @@ class EngineT : public Engine {
     Status launch_col(int first, int count, bool level1) {
         if constexpr (wr_ok_) {
             if (!level1 && colwr_) {
+                if (count > kMaxColGroups) return Status::err(FFTLB_ERR_ARG, "too many column groups in one launch");
 #define FFTLB_KCOLWR(NYV)                                                                                     \
     kcol_wr<NYV><<<gridcw_, ntcw_, smemcw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_, kp_, BOXR_, \
                                                        nbufcw_, tmap_convw_, err_)
@@ -1792,6 +1835,7 @@ class EngineT : public Engine {
                 return Status::ok();
             }
             if (level1 && colmwr_) {
+                if (count > kMaxMGroups) return Status::err(FFTLB_ERR_ARG, "too many column groups in one launch");
 #define FFTLB_KCOLMWR(NYV)                                                                                    \
     kcolm_wr<NYV><<<gridcmw_, ntcw_, smemcmw_, stream_>>>(specb_, groups_ + first, count, kxt_, kyt_, Twc_, kp_,   \
                                                           BOXR_, tmap_convw_, err_)
@@ -1860,23 +1904,23 @@ class EngineT : public Engine {
             if (k3wr_) {
                 const int nt = nt_wr_host(h_);
                 if (h_ == 512)
-                    k3_wr<512><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                    k3_wr<512><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kxt_, kp_, err_);
                 else if (h_ == 256)
-                    k3_wr<256><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                    k3_wr<256><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kxt_, kp_, err_);
                 else
-                    k3_wr<128><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kp_, err_);
+                    k3_wr<128><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kxt_, kp_, err_);
                 k3done = true;
             }
         }
         if (!k3done) {
             const int ml = row_maxlr(WR3_, NT3);
             k3_pipe<real, SPLIT><<<B_ * ny_, NT3, smem3_, stream_>>>(specb_, fieldsb_, auxb_, Wr_, Wp_, ml == 3 ? Tr8_ : Tr_,
-                                                              ml == 3 ? ntr8_ : ntr_, kp_, WR3_, ml, err_);
+                                                              ml == 3 ? ntr8_ : ntr_, kxt_, kp_, WR3_, ml, err_);
         }
         FFTLB_LAUNCHED("k3_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL2)).good()) return st;
-        if (!(st = launch_col(l2_groups_, 3, true)).good()) return st;
+        if (!(st = launch_col(l2_groups_, 3, false)).good()) return st;   // one input, one output each
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_FINAL)).good()) return st;
         if constexpr (wr_ok_) {

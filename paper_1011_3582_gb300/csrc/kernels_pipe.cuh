@@ -396,13 +396,24 @@ __host__ __device__ __forceinline__ size_t tile_stride(int TW, int ny) {
     return bytes / sizeof(C);
 }
 
-template <typename C>
-__device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDesc *groups, int k, int ntiles,
+// The fields of a group that the tile copies and a one-input job read,
+// staged in shared memory once per launch by the warp-resident column
+// kernels (a per-job copy of the whole GroupDesc by one thread held every
+// other warp of the block at the next barrier).
+struct ColG {
+    int nin, in_slot[2], out_slot, add_slot;
+    float c0, c1;
+};
+constexpr int kMaxColGroups = 32;   // groups of one kcol_wr launch (32 convection groups)
+
+// (GD: GroupDesc in global memory, or ColG / GroupDesc staged in shared memory)
+template <typename C, typename GD>
+__device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GD *groups, int k, int ntiles,
                                            int ngroups, int TW, int ny, int BOXR, const CUtensorMap *tmap) {
     const int job = (int)blockIdx.x + k * (int)gridDim.x;
     const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
     const int g = jr / ntiles, t = jr - g * ntiles;
-    const GroupDesc *G = groups + g;
+    const GD *G = groups + g;
     const int nin = G->nin;
     const int tile = TW * ny;
     mbar_expect_tx(bar, (uint32_t)(nin * tile * sizeof(C)));
@@ -411,15 +422,20 @@ __device__ __forceinline__ void kcol_issue(C *dst, uint64_t *bar, const GroupDes
         for (int r0 = 0; r0 < ny; r0 += BOXR)
             tma_load_2d(dst + (size_t)s * tile_stride<C>(TW, ny) + (size_t)r0 * TW, tmap, 2 * t * TW, sl * ny + r0, bar);
     }
+    if (G->add_slot >= 0) {   // the addend tile, read at the job's store: into L2 now
+        const int sl = run * NSLOT + G->add_slot;
+        for (int r0 = 0; r0 < ny; r0 += BOXR) tma_prefetch_2d(tmap, 2 * t * TW, sl * ny + r0);
+    }
 }
 
 // L2 prefetch of the tiles kcol_issue would load for job k
-__device__ __forceinline__ void kcol_prefetch(const GroupDesc *groups, int k, int ntiles, int ngroups, int TW, int ny,
+template <typename GD>
+__device__ __forceinline__ void kcol_prefetch(const GD *groups, int k, int ntiles, int ngroups, int TW, int ny,
                                               int BOXR, const CUtensorMap *tmap) {
     const int job = (int)blockIdx.x + k * (int)gridDim.x;
     const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
     const int g = jr / ntiles, t = jr - g * ntiles;
-    const GroupDesc *G = groups + g;
+    const GD *G = groups + g;
     for (int s = 0; s < G->nin; ++s) {
         const int sl = run * NSLOT + G->in_slot[s];
         for (int r0 = 0; r0 < ny; r0 += BOXR) tma_prefetch_2d(tmap, 2 * t * TW, sl * ny + r0);
@@ -536,9 +552,28 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
                 lr = w2 ? ly : lx;
             }
             gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0;
-            for (int idx = tid; idx < tile; idx += NT) {
-                const int e = idx >> lgTW, c = idx & (TW - 1);
-                gout[(size_t)e * h + c] = R[lr(c, e)];
+            if (gd.add_slot >= 0) {   // plus the term the row kernel formed
+                // (8 loads before their stores: gout may alias ad, so a load
+                // after a store could not be issued ahead of it)
+                const C *ad = spec_r + (size_t)gd.add_slot * slot + kx0;
+                for (int i0 = tid; i0 < tile; i0 += 8 * NT) {
+                    C a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = i0 + u * NT, e = idx >> lgTW, c = idx & (TW - 1);
+                        if (idx < tile) a[u] = ad[(size_t)e * h + c];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = i0 + u * NT, e = idx >> lgTW, c = idx & (TW - 1);
+                        if (idx < tile) gout[(size_t)e * h + c] = cadd(R[lr(c, e)], a[u]);
+                    }
+                }
+            } else {
+                for (int idx = tid; idx < tile; idx += NT) {
+                    const int e = idx >> lgTW, c = idx & (TW - 1);
+                    gout[(size_t)e * h + c] = R[lr(c, e)];
+                }
             }
         } else {
             C *in1 = in0 + tstr;
@@ -628,13 +663,41 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
 
 constexpr int NT3 = 256;
 
+// i m z
+template <typename real, typename C>
+__device__ __forceinline__ C imul(real m, C z) { return C{-m * z.y, m * z.x}; }
+
+// The level-1 derivatives K3 forms in the row spectrum (k3_src_slot), at
+// bin k of the one-sided rows of d (row o at d + o rs; bin 0 carries DC and
+// row-Nyquist, both with k_x = 0): row D_RX holds rho^, D_UXX u_x^, D_UYX
+// u_y^, D_TX T^, D_PIX Pi^, D_GX g^ as loaded; D_LAP holds d_yy rho and
+// D_UYY d_y u_y from the column pass.  ax = k_x of bin k, sx = 1 / nx.
+template <typename real, typename C>
+__device__ __forceinline__ void k3_form_x(C *d, int rs, int k, real ax, real sx) {
+    const real m = ax * sx;
+    const C r = d[D_RX * rs + k];
+    C lap = d[D_LAP * rs + k];
+    lap.x -= ax * m * r.x;
+    lap.y -= ax * m * r.y;
+    d[D_LAP * rs + k] = lap;                          // (d_xx + d_yy) rho
+    d[D_RX * rs + k] = imul(m, r);                    // d_x rho
+    const C uxx = imul(m, d[D_UXX * rs + k]);
+    d[D_UXX * rs + k] = uxx;                          // d_x u_x
+    d[D_DIVX * rs + k] = imul(ax, cadd(uxx, d[D_UYY * rs + k]));   // d_x (d_x u_x + d_y u_y)
+    d[D_UYX * rs + k] = imul(m, d[D_UYX * rs + k]);   // d_x u_y
+    d[D_TX * rs + k] = imul(m, d[D_TX * rs + k]);
+    d[D_PIX * rs + k] = imul(m, d[D_PIX * rs + k]);
+    d[D_GX * rs + k] = imul(m, d[D_GX * rs + k]);
+}
+
 template <typename real, bool TC = false>
 __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spec, const real *__restrict__ fields,
                                                real *__restrict__ aux,
                                                const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                const typename cplx_of<real>::type *__restrict__ Tr_g, int ntr,
-                                               KP<real> P, int WR, int maxlr, int *err) {
+                                               const real *__restrict__ kxt, KP<real> P, int WR, int maxlr,
+                                               int *err) {
     const uint4 *tc = TC ? P.tc16 : nullptr;   // split-BF16 tensor-core first passes
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -661,9 +724,10 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     }
     __syncthreads();   // the barrier is initialised before any thread polls it
     if (tid == 0) {
-        mbar_expect_tx(&bar, (uint32_t)(ND1 + 2) * rowbytes);
+        mbar_expect_tx(&bar, (uint32_t)(ND1 + 1) * rowbytes);   // D_DIVX is formed here
         for (int o = 0; o < ND1; ++o)
-            bulk_g2s(d + (size_t)o * h, spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h, rowbytes, &bar);
+            if (k3_src_slot(o) >= 0)
+                bulk_g2s(d + (size_t)o * h, spec + (size_t)k3_src_slot(o) * slot + (size_t)y * h, rowbytes, &bar);
         bulk_g2s(rT, fields + (size_t)y * nx, rowbytes, &bar);
         bulk_g2s(rT + nx, fields + 3 * N + (size_t)y * nx, rowbytes, &bar);
     }
@@ -674,6 +738,8 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
         mbar_wait_bounded(&bar, 0);
         return;
     }
+    for (int k = tid; k < h; k += NT3) k3_form_x<real>(d, h, k, kxt[k], P.scale_x);
+    __syncthreads();
     c2r_pre_l(d, la, h, ND1, Wp, tid, NT3);
     __syncthreads();
     rows_fft_to_A<+1>(d, la, wk, lb, h, ND1, WR, Wr, Tr, NT3, maxlr, tc);
@@ -719,8 +785,13 @@ __global__ void __launch_bounds__(NT3) k3_pipe(typename cplx_of<real>::type *spe
     r2c_post_l(res2, lr2, h, 5, Wp, tid, NT3);
     __syncthreads();
     for (int r = 0; r < 5; ++r) {
-        C *dst = spec + (size_t)(SLOT_L2 + r) * slot + (size_t)y * h;
-        for (int k = tid; k < h; k += NT3) dst[k] = res2[lr2(r, k)];
+        C *raw = k3_raw_slot(r) >= 0 ? spec + (size_t)k3_raw_slot(r) * slot + (size_t)y * h : nullptr;
+        C *mul = k3_mul_slot(r) >= 0 ? spec + (size_t)k3_mul_slot(r) * slot + (size_t)y * h : nullptr;
+        for (int k = tid; k < h; k += NT3) {
+            const C X = res2[lr2(r, k)];
+            if (raw) raw[k] = X;
+            if (mul) mul[k] = imul(kxt[k] * P.scale_x, X);   // the d_x term of level 2
+        }
     }
 }
 

@@ -215,6 +215,41 @@ __device__ __forceinline__ void r2c_post_wr(const C *z, C *out, const C *Wp, int
     }
 }
 
+// r2c_post_wr with two destinations: X to raw and i k_x X / nx (the d_x
+// term of a level-2 output) to mul; either may be null.  kxt[k] = k_x of
+// bin k, sx = 1 / nx; bin 0 (DC, row-Nyquist) has k_x = 0 for both.
+template <int H, typename C>
+__device__ __forceinline__ void r2c_post_wr2(const C *z, C *raw, C *mul, const float *__restrict__ kxt, float sx,
+                                             const C *Wp, int j) {
+    using R = decltype(z[0].x);
+    constexpr int P = RowCfg<H>::P;
+#pragma unroll
+    for (int k0 = 0; k0 <= H / 2; k0 += P) {
+        const int k = k0 + j;
+        if (k > H / 2) break;
+        C a, b;
+        if (k == 0) {
+            const C z0 = z[0];
+            a = C{z0.x + z0.y, z0.x - z0.y};
+        } else {
+            const C p = z[k], q = z[H - k];
+            const C ze = cscale(cadd(p, cconj(q)), R(0.5));
+            const C zo = cscale(cmul_mi(csub(p, cconj(q))), R(0.5));
+            const C wz = cmul(Wp[k], zo);
+            a = cadd(ze, wz);
+            b = cconj(csub(ze, wz));
+        }
+        if (raw) {
+            raw[k] = a;
+            if (k != 0 && H - k != k) raw[H - k] = b;
+        }
+        if (mul) {
+            mul[k] = imul(kxt[k] * sx, a);
+            if (k != 0 && H - k != k) mul[H - k] = imul(kxt[H - k] * sx, b);
+        }
+    }
+}
+
 // Inverse real rows, in place: one-sided packed spectrum X -> Z[k] = (X[k]
 // + X[k + H]) + i (X[k] - X[k + H]) exp(+2 pi i k / 2H), X[k + H] =
 // conj X[H - k]; the half-length inverse of Z is the real row.
@@ -406,9 +441,10 @@ __device__ __forceinline__ void k3_issue(const typename cplx_of<real>::type *spe
     spec += (size_t)run * NSLOT * slot;
     fields += (size_t)run * 4 * N;
     const uint32_t rowbytes = (uint32_t)(nx * sizeof(real));
-    mbar_expect_tx(bar, (uint32_t)(ND1 + 2) * rowbytes);
+    mbar_expect_tx(bar, (uint32_t)(ND1 + 1) * rowbytes);   // D_DIVX is formed in K3
     for (int o = 0; o < ND1; ++o)
-        bulk_g2s(dst + (size_t)o * nx, spec + (size_t)(SLOT_D1 + o) * slot + (size_t)y * h, rowbytes, bar);
+        if (k3_src_slot(o) >= 0)
+            bulk_g2s(dst + (size_t)o * nx, spec + (size_t)k3_src_slot(o) * slot + (size_t)y * h, rowbytes, bar);
     bulk_g2s(dst + (size_t)ND1 * nx, fields + (size_t)y * nx, rowbytes, bar);
     bulk_g2s(dst + (size_t)(ND1 + 1) * nx, fields + 3 * N + (size_t)y * nx, rowbytes, bar);
 }
@@ -416,10 +452,11 @@ __device__ __forceinline__ void k3_issue(const typename cplx_of<real>::type *spe
 template <int H>
 __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *spec, const float *__restrict__ fields,
                                                  float *__restrict__ aux, const float2 *__restrict__ tw_g,
-                                                 const float2 *__restrict__ Wp_g, KP<float> P, int *err) {
+                                                 const float2 *__restrict__ Wp_g, const float *__restrict__ kxt,
+                                                 KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = nt_wr<H>(), NWARP = NT / 32;
+    constexpr int NX = 2 * H, NT = nt_wr<H>();
     constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
     constexpr int SMAX = (NX + NT - 1) / NT;
     constexpr int RB = ND1 + 2;   // rows per buffer
@@ -470,6 +507,8 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
             pend0 = false;
         }
         real *d = odd ? buf1 : buf0;
+        for (int k = tid; k < H; k += NT) k3_form_x<real>(reinterpret_cast<C *>(d), H, k, kxt[k], P.scale_x);
+        __syncthreads();
         if (grp < ND1) {
             C *zr = reinterpret_cast<C *>(d) + (size_t)grp * H;
             c2r_pre_wr<H>(zr, Wp, j);
@@ -515,7 +554,9 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
         if (grp < 5) {
             C *zr = reinterpret_cast<C *>(d) + (size_t)grp * H;
             row_fft_wr<H, -1>(zr, tw, j, rsw);
-            r2c_post_wr<H>(zr, spec_r + (size_t)(SLOT_L2 + grp) * slot + (size_t)y * H, Wp, j);
+            C *raw = k3_raw_slot(grp) >= 0 ? spec_r + (size_t)k3_raw_slot(grp) * slot + (size_t)y * H : nullptr;
+            C *mul = k3_mul_slot(grp) >= 0 ? spec_r + (size_t)k3_mul_slot(grp) * slot + (size_t)y * H : nullptr;
+            r2c_post_wr2<H>(zr, raw, mul, kxt, P.scale_x, Wp, j);
         }
         fence_proxy_async();
         __syncthreads();
@@ -819,7 +860,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
     constexpr int E = ColCfg<NY>::E, PP = ColCfg<NY>::P, TW = ColCfg<NY>::TW, NT = TW * PP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar0, bar1;
-    __shared__ GroupDesc gd;
+    __shared__ ColG gt[kMaxColGroups];   // ngroups <= kMaxColGroups (checked by the host)
     const int h = P.h, tid = threadIdx.x;
     const int c = tid % TW, jl = tid / TW;
     const size_t slot = (size_t)NY * h;
@@ -842,11 +883,16 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
     load_tab(twc, twc_g, 2 * NY, NT);
     load_tab(kxs, kxt, h + 1, NT);
     load_tab(kys, kyt, NY, NT);
+    for (int g = tid; g < ngroups; g += NT) {
+        const GroupDesc &G = groups[g];
+        gt[g] = ColG{G.nin, {G.in_slot[0], G.in_slot[1]}, G.out_slot[0], G.add_slot, (float)G.c[0][0][0],
+                     (float)G.c[0][0][1]};
+    }
     __syncthreads();
     if (tid == 0) {
-        if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
-        if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
-        if (njobs > nbuf) kcol_prefetch(groups, nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (njobs > 0) kcol_issue(buf0, &bar0, gt, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, gt, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (njobs > nbuf) kcol_prefetch(gt, nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
     }
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1;
@@ -858,7 +904,6 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
         const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
         const int g = jr / ntiles, t = jr - g * ntiles;
         const int kx0 = t * TW;
-        if (tid == 0) gd = groups[g];
         if (!block_wait(bar, odd ? par1 : par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
             if (pend1) mbar_wait_bounded(&bar1, par1);
@@ -872,11 +917,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
             pend0 = false;
         }
         C *T = odd ? buf1 : buf0;
-        // (the group's fields are read before the next job's thread 0 can
-        // overwrite gd: after this job's last block barrier only registers
-        // are used)
-        const int oslot = gd.out_slot[0];
-        const real c0 = (real)gd.c[0][0][0], c1 = (real)gd.c[0][0][1];
+        const int oslot = gt[g].out_slot, aslot = gt[g].add_slot;
+        const real c0 = gt[g].c0, c1 = gt[g].c1;
         C v[E];
         // stage 1, forward
 #pragma unroll
@@ -916,16 +958,30 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
         __syncthreads();
         if (tid == 0 && k + nbuf < njobs) {   // the tile buffer is free: prefetch job k + nbuf into it
             const bool nodd = (k + nbuf) & 1;
-            kcol_issue(T, nodd ? &bar1 : &bar0, groups, k + nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
+            kcol_issue(T, nodd ? &bar1 : &bar0, gt, k + nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
             if (nodd) pend1 = true;
             else pend0 = true;
             // and the job after it into L2, so that its copy finds the tiles there
-            if (k + nbuf + 1 < njobs) kcol_prefetch(groups, k + nbuf + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+            if (k + nbuf + 1 < njobs) kcol_prefetch(gt, k + nbuf + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
         }
         SmallDFT<E, +1, C>::run(v);
         C *out = spec + (size_t)run * NSLOT * slot + (size_t)oslot * slot + kx0 + c;
+        if (aslot >= 0) {   // plus the term the row kernel formed (its tile was prefetched into L2)
+            // (8 loads before their 8 stores: out may alias ad, so no load
+            // can be issued ahead of an earlier store)
+            const C *ad = spec + (size_t)run * NSLOT * slot + (size_t)aslot * slot + kx0 + c;
 #pragma unroll
-        for (int q = 0; q < E; ++q) out[(size_t)(jl + PP * q) * h] = v[q];
+            for (int q0 = 0; q0 < E; q0 += 8) {
+                C a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = ad[(size_t)(jl + PP * (q0 + u)) * h];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) out[(size_t)(jl + PP * (q0 + u)) * h] = cadd(v[q0 + u], a[u]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < E; ++q) out[(size_t)(jl + PP * q) * h] = v[q];
+        }
     }
 }
 
@@ -938,6 +994,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
 // stage 2 and the conjugate twiddles into the work tile, a block barrier,
 // the inverse stage 1 and the global store, a block barrier.  The next job's
 // input tiles are fetched as soon as the last output has read them.
+constexpr int kMaxMGroups = 8;   // groups of one kcolm_wr launch (5 level-1 groups)
+
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(float2 *spec,
                                                                               const GroupDesc *__restrict__ groups,
@@ -954,7 +1012,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
     constexpr int NQ = E / PP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar0;
-    __shared__ GroupDesc gd;
+    __shared__ GroupDesc gs[kMaxMGroups];   // the launch's groups (ngroups <= kMaxMGroups, checked by the host)
     const int h = P.h, tid = threadIdx.x;
     const int c = tid % TW, jl = tid / TW;
     const size_t slot = (size_t)NY * h;
@@ -976,9 +1034,15 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
     load_tab(twc, twc_g, 2 * NY, NT);
     load_tab(kxs, kxt, h + 1, NT);
     load_tab(kys, kyt, NY, NT);
+    {
+        const int nw = ngroups * (int)(sizeof(GroupDesc) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(groups);
+        int *dst = reinterpret_cast<int *>(gs);
+        for (int i = tid; i < nw; i += NT) dst[i] = src[i];
+    }
     __syncthreads();
-    if (tid == 0 && njobs > 0) kcol_issue(in, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
-    if (tid == 0 && njobs > 1) kcol_prefetch(groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+    if (tid == 0 && njobs > 0) kcol_issue(in, &bar0, gs, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+    if (tid == 0 && njobs > 1) kcol_prefetch(gs, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
     uint32_t par0 = 0;
     bool pend0 = njobs > 0;
     const real scale = P.scale;
@@ -987,7 +1051,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
         const int run = job / (ngroups * ntiles), jr = job - run * ngroups * ntiles;
         const int g = jr / ntiles, t = jr - g * ntiles;
         const int kx0 = t * TW;
-        if (tid == 0) gd = groups[g];
+        const GroupDesc &gd = gs[g];
         if (!block_wait(&bar0, par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
             return;
@@ -1054,9 +1118,9 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
             if (last) fence_proxy_async();
             __syncthreads();
             if (last && tid == 0 && k + 1 < njobs) {   // the input tiles are free: fetch the next job's
-                kcol_issue(in, &bar0, groups, k + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+                kcol_issue(in, &bar0, gs, k + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
                 pend0 = true;
-                if (k + 2 < njobs) kcol_prefetch(groups, k + 2, ntiles, ngroups, TW, NY, BOXR, &tmap);
+                if (k + 2 < njobs) kcol_prefetch(gs, k + 2, ntiles, ngroups, TW, NY, BOXR, &tmap);
             }
             C v[E];
 #pragma unroll
