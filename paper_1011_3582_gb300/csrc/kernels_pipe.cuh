@@ -96,6 +96,22 @@ __device__ __forceinline__ void load_tab(C *dst, const C *src, int n, int nthr) 
     for (int i = threadIdx.x; i < n; i += nthr) dst[i] = src[i];
 }
 
+// load_tab with four loads in flight before their stores (a store to the
+// generic pointer dst would otherwise hold back the next load): for kernels
+// whose prologue is on the critical path of a short launch
+template <typename C>
+__device__ __forceinline__ void load_tab4(C *dst, const C *__restrict__ src, int n, int nthr) {
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * nthr) {
+        C v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * nthr < n) v[u] = __ldg(src + i0 + u * nthr);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * nthr < n) dst[i0 + u * nthr] = v[u];
+    }
+}
+
 // real value x of row r of a packed-complex row buffer in layout L
 template <typename real>
 __device__ __forceinline__ real real_at(const typename cplx_of<real>::type *buf, Lay L, int r, int x) {
@@ -507,7 +523,13 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
         const int g = jr / ntiles, t = jr - g * ntiles;
         const int kx0 = t * TW;
         C *spec_r = spec + (size_t)run * NSLOT * slot;
-        if (tid == 0) gd = groups[g];
+        {   // the group's descriptor, one word per thread (the previous job's last
+            // reads of gd came before its final block barrier; block_wait below
+            // orders these writes before the first read)
+            const int *src = reinterpret_cast<const int *>(groups + g);
+            int *dst = reinterpret_cast<int *>(&gd);
+            for (int i = tid; i < (int)(sizeof(GroupDesc) / sizeof(int)); i += NT) dst[i] = src[i];
+        }
         if (!block_wait(bar, odd ? par1 : par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
             if (pend1) mbar_wait_bounded(&bar1, par1);
@@ -553,18 +575,18 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
             }
             gout = spec_r + (size_t)gd.out_slot[0] * slot + kx0;
             if (gd.add_slot >= 0) {   // plus the term the row kernel formed
-                // (8 loads before their stores: gout may alias ad, so a load
+                // (4 loads before their stores: gout may alias ad, so a load
                 // after a store could not be issued ahead of it)
                 const C *ad = spec_r + (size_t)gd.add_slot * slot + kx0;
-                for (int i0 = tid; i0 < tile; i0 += 8 * NT) {
-                    C a[8];
+                for (int i0 = tid; i0 < tile; i0 += 4 * NT) {
+                    C a[4];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < 4; ++u) {
                         const int idx = i0 + u * NT, e = idx >> lgTW, c = idx & (TW - 1);
                         if (idx < tile) a[u] = ad[(size_t)e * h + c];
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < 4; ++u) {
                         const int idx = i0 + u * NT, e = idx >> lgTW, c = idx & (TW - 1);
                         if (idx < tile) gout[(size_t)e * h + c] = cadd(R[lr(c, e)], a[u]);
                     }

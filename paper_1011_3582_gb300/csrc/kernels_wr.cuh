@@ -313,18 +313,16 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const floa
     const int NY = P.nrun * ny;
     const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int njobs = nrows * NCH;
-    if (tid == 0) {
+    if (tid == 0) {   // (the first copies start before the tables load)
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
         mbar_init_fence();
-    }
-    load_tab(tw, tw_g, H, NT);
-    load_tab(Wp, Wp_g, H / 2 + 1, NT);
-    __syncthreads();
-    if (tid == 0) {
         if (njobs > 0) k1_issue(f, buf0, &bar0, 0, NCH, CH, nx, ny, N);
         if (njobs > 1) k1_issue(f, buf1, &bar1, 1, NCH, CH, nx, ny, N);
     }
+    load_tab4(tw, tw_g, H, NT);
+    load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    __syncthreads();
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1;
     real a0[SMAX], a1[SMAX], a2[SMAX], a3[SMAX];
@@ -473,18 +471,16 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
     real *buf1 = (real *)sc.take((size_t)RB * NX * sizeof(real));
     const int NY = P.nrun * ny;
     const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    if (tid == 0) {
+    if (tid == 0) {   // (the first copies start before the tables load)
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
         mbar_init_fence();
-    }
-    load_tab(tw, tw_g, H, NT);
-    load_tab(Wp, Wp_g, H / 2 + 1, NT);
-    __syncthreads();
-    if (tid == 0) {
         if (nrows > 0) k3_issue<real>(spec, fields, buf0, &bar0, 0, nx, ny, N, slot, H);
         if (nrows > 1) k3_issue<real>(spec, fields, buf1, &bar1, 1, nx, ny, N, slot, H);
     }
+    load_tab4(tw, tw_g, H, NT);
+    load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    __syncthreads();
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = nrows > 0, pend1 = nrows > 1;
     for (int ri = 0; ri < nrows; ++ri) {
@@ -615,22 +611,20 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
     const int NY = P.nrun * ny;
     const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int njobs = nrows * NCH;
-    if (tid == 0) {
+    if (tid == 0) {   // (the first copies start before the tables load)
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
         mbar_init(&hbar0, 1);
         mbar_init(&hbar1, 1);
         mbar_init_fence();
-    }
-    load_tab(tw, tw_g, H, NT);
-    load_tab(Wp, Wp_g, H / 2 + 1, NT);
-    __syncthreads();
-    if (tid == 0) {
         if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, H);
         if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, H);
         if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, NCH, CH, nx, ny, slot, H);
         if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, NCH, CH, nx, ny, slot, H);
     }
+    load_tab4(tw, tw_g, H, NT);
+    load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    __syncthreads();
     uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
     const real dt = P.dt, itau = real(1) / P.tau;
@@ -859,7 +853,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
     using real = float;
     constexpr int E = ColCfg<NY>::E, PP = ColCfg<NY>::P, TW = ColCfg<NY>::TW, NT = TW * PP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar0, bar1;
+    __shared__ __align__(8) uint64_t bar0, bar1, abar;
     __shared__ ColG gt[kMaxColGroups];   // ngroups <= kMaxColGroups (checked by the host)
     const int h = P.h, tid = threadIdx.x;
     const int c = tid % TW, jl = tid / TW;
@@ -875,26 +869,25 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
     const int ntiles = h / TW;
     const int njobs_total = P.nrun * ngroups * ntiles;
     const int njobs = (int)blockIdx.x < njobs_total ? (njobs_total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    if (tid == 0) {
+    if (tid == 0) {   // (the first copies start before the tables load)
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
+        mbar_init(&abar, 1);
         mbar_init_fence();
+        if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (njobs > nbuf) kcol_prefetch(groups, nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
     }
-    load_tab(twc, twc_g, 2 * NY, NT);
-    load_tab(kxs, kxt, h + 1, NT);
-    load_tab(kys, kyt, NY, NT);
+    load_tab4(twc, twc_g, 2 * NY, NT);
+    load_tab4(kxs, kxt, h + 1, NT);
+    load_tab4(kys, kyt, NY, NT);
     for (int g = tid; g < ngroups; g += NT) {
         const GroupDesc &G = groups[g];
         gt[g] = ColG{G.nin, {G.in_slot[0], G.in_slot[1]}, G.out_slot[0], G.add_slot, (float)G.c[0][0][0],
                      (float)G.c[0][0][1]};
     }
     __syncthreads();
-    if (tid == 0) {
-        if (njobs > 0) kcol_issue(buf0, &bar0, gt, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
-        if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, gt, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
-        if (njobs > nbuf) kcol_prefetch(gt, nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
-    }
-    uint32_t par0 = 0, par1 = 0;
+    uint32_t par0 = 0, par1 = 0, apar = 0;
     bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1;
     const real scale = P.scale;
     for (int k = 0; k < njobs; ++k) {
@@ -956,7 +949,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
         for (int k1 = 0; k1 < E; ++k1) v[k1] = T[cpos<NY>(c, jl, k1)];
         fence_proxy_async();
         __syncthreads();
-        if (tid == 0 && k + nbuf < njobs) {   // the tile buffer is free: prefetch job k + nbuf into it
+        // the tile buffer is free: with an addend, its tile comes into the
+        // buffer first (read after the inverse DFT), then the next job's
+        if (tid == 0 && aslot >= 0) {
+            const int sl = run * NSLOT + aslot;
+            mbar_expect_tx(&abar, (uint32_t)(tile * sizeof(C)));
+            for (int r0 = 0; r0 < NY; r0 += BOXR) tma_load_2d(T + (size_t)r0 * TW, &tmap, 2 * t * TW, sl * NY + r0, &abar);
+        }
+        if (tid == 0 && aslot < 0 && k + nbuf < njobs) {   // prefetch job k + nbuf into the buffer
             const bool nodd = (k + nbuf) & 1;
             kcol_issue(T, nodd ? &bar1 : &bar0, gt, k + nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
             if (nodd) pend1 = true;
@@ -966,17 +966,24 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
         }
         SmallDFT<E, +1, C>::run(v);
         C *out = spec + (size_t)run * NSLOT * slot + (size_t)oslot * slot + kx0 + c;
-        if (aslot >= 0) {   // plus the term the row kernel formed (its tile was prefetched into L2)
-            // (8 loads before their 8 stores: out may alias ad, so no load
-            // can be issued ahead of an earlier store)
-            const C *ad = spec + (size_t)run * NSLOT * slot + (size_t)aslot * slot + kx0 + c;
+        if (aslot >= 0) {   // plus the term the row kernel formed
+            if (!block_wait(&abar, apar, err)) {
+                mbar_wait_bounded(&abar, apar);
+                if (pend0) mbar_wait_bounded(&bar0, par0);
+                if (pend1) mbar_wait_bounded(&bar1, par1);
+                return;
+            }
+            apar ^= 1;
 #pragma unroll
-            for (int q0 = 0; q0 < E; q0 += 8) {
-                C a[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) a[u] = ad[(size_t)(jl + PP * (q0 + u)) * h];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) out[(size_t)(jl + PP * (q0 + u)) * h] = cadd(v[q0 + u], a[u]);
+            for (int q = 0; q < E; ++q) out[(size_t)(jl + PP * q) * h] = cadd(v[q], T[(jl + PP * q) * TW + c]);
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0 && k + nbuf < njobs) {
+                const bool nodd = (k + nbuf) & 1;
+                kcol_issue(T, nodd ? &bar1 : &bar0, gt, k + nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
+                if (nodd) pend1 = true;
+                else pend0 = true;
+                if (k + nbuf + 1 < njobs) kcol_prefetch(gt, k + nbuf + 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
             }
         } else {
 #pragma unroll
@@ -1027,13 +1034,15 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
     const int ntiles = h / TW;
     const int njobs_total = P.nrun * ngroups * ntiles;
     const int njobs = (int)blockIdx.x < njobs_total ? (njobs_total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    if (tid == 0) {
+    if (tid == 0) {   // (the first copies start before the tables load)
         mbar_init(&bar0, 1);
         mbar_init_fence();
+        if (njobs > 0) kcol_issue(in, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
+        if (njobs > 1) kcol_prefetch(groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
     }
-    load_tab(twc, twc_g, 2 * NY, NT);
-    load_tab(kxs, kxt, h + 1, NT);
-    load_tab(kys, kyt, NY, NT);
+    load_tab4(twc, twc_g, 2 * NY, NT);
+    load_tab4(kxs, kxt, h + 1, NT);
+    load_tab4(kys, kyt, NY, NT);
     {
         const int nw = ngroups * (int)(sizeof(GroupDesc) / sizeof(int));
         const int *src = reinterpret_cast<const int *>(groups);
@@ -1041,8 +1050,6 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
         for (int i = tid; i < nw; i += NT) dst[i] = src[i];
     }
     __syncthreads();
-    if (tid == 0 && njobs > 0) kcol_issue(in, &bar0, gs, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
-    if (tid == 0 && njobs > 1) kcol_prefetch(gs, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
     uint32_t par0 = 0;
     bool pend0 = njobs > 0;
     const real scale = P.scale;
