@@ -1566,7 +1566,7 @@ class EngineT : public Engine {
             }
             if (rows && k3_wr_smem(h_) <= budget_) {
                 smem3w_ = k3_wr_smem(h_);
-                st = h_ == 512 ? occupancy(k3_wr<512>, NTr, smem3w_, &nb)
+                st = h_ == 512 ? occupancy(k3_wr<512>, nt_k3wr_host(h_), smem3w_, &nb)
                    : h_ == 256 ? occupancy(k3_wr<256>, NTr, smem3w_, &nb)
                                : occupancy(k3_wr<128>, NTr, smem3w_, &nb);
                 if (!st.good()) return st;
@@ -1577,7 +1577,7 @@ class EngineT : public Engine {
             }
             if (rows && k1_wr_smem(h_) <= budget_) {
                 smem1w_ = k1_wr_smem(h_);
-                st = h_ == 512 ? occupancy(k1_wr<512>, NTr, smem1w_, &nb)
+                st = h_ == 512 ? occupancy(k1_wr<512>, nt_k1wr_host(h_), smem1w_, &nb)
                    : h_ == 256 ? occupancy(k1_wr<256>, NTr, smem1w_, &nb)
                                : occupancy(k1_wr<128>, NTr, smem1w_, &nb);
                 if (!st.good()) return st;
@@ -1869,7 +1869,7 @@ class EngineT : public Engine {
         bool k1done = false;
         if constexpr (wr_ok_) {
             if (k1wr_) {
-                const int nt = nt_wr_host(h_);
+                const int nt = nt_k1wr_host(h_);
                 if (h_ == 512)
                     k1_wr<512><<<grid1w_, nt, smem1w_, stream_>>>(cur, specb_, fieldsb_, Tw1_, Wp_, kp_, err_);
                 else if (h_ == 256)
@@ -1902,7 +1902,7 @@ class EngineT : public Engine {
         bool k3done = false;
         if constexpr (wr_ok_) {
             if (k3wr_) {
-                const int nt = nt_wr_host(h_);
+                const int nt = nt_k3wr_host(h_);
                 if (h_ == 512)
                     k3_wr<512><<<grid3w_, nt, smem3w_, stream_>>>(specb_, fieldsb_, auxb_, Tw1_, Wp_, kxt_, kp_, err_);
                 else if (h_ == 256)

@@ -88,6 +88,24 @@ template <> struct RowCfg<128> { static constexpr int E = 16, P = 8; };
 #endif
 template <int H> __host__ __device__ constexpr int nt_wr() { return H >= 256 ? 512 : 256; }
 inline int nt_wr_host(int H) { return H >= 256 ? 512 : 256; }
+// Threads of the forward row kernel at H = 512: 256, i.e. two blocks per
+// SM, each with 8-row chunks (measured at 1024^2: 68.7 us against 83.3 us
+// for one 512-thread block with 16-row chunks; FFTLB_K1_NT512 selects 512)
+#ifndef FFTLB_K1_NT512
+#define FFTLB_K1_NT512 256
+#endif
+template <int H> __host__ __device__ constexpr int nt_k1wr() { return H == 512 ? FFTLB_K1_NT512 : nt_wr<H>(); }
+inline int nt_k1wr_host(int H) { return H == 512 ? FFTLB_K1_NT512 : nt_wr_host(H); }
+// Threads of the level-1 row kernel at H = 512: 256 with one row buffer,
+// i.e. two blocks per SM (measured at 1024^2: 39.3 us against 46.4 us for
+// one 512-thread block with two row buffers; FFTLB_K3_NT512 selects 512)
+#ifndef FFTLB_K3_NT512
+#define FFTLB_K3_NT512 256
+#endif
+template <int H> __host__ __device__ constexpr int nt_k3wr() { return H == 512 ? FFTLB_K3_NT512 : nt_wr<H>(); }
+inline int nt_k3wr_host(int H) { return H == 512 ? FFTLB_K3_NT512 : nt_wr_host(H); }
+template <int H> __host__ __device__ constexpr int nb_k3wr() { return nt_k3wr<H>() == 512 || H < 256 ? 2 : 1; }
+inline int nb_k3wr_host(int H) { return nt_k3wr_host(H) == 512 || H < 256 ? 2 : 1; }
 template <int H> __host__ __device__ constexpr int nt_k5wr() { return H == 512 ? FFTLB_K5_NT512 : nt_wr<H>(); }
 inline int nt_k5wr_host(int H) { return H == 512 ? FFTLB_K5_NT512 : nt_wr_host(H); }
 // head buffers of the final row kernel: two (the next row's head fetched a
@@ -286,13 +304,31 @@ __device__ __forceinline__ void c2r_pre_wr(C *z, const C *Wp, int j) {
 // pass (one per row group), two chunk buffers.
 // ---------------------------------------------------------------------------
 
+// the distribution rows of chunk c of a row: the rest velocity and the
+// first NG moving rows, then NG moving rows per chunk
+__host__ __device__ constexpr int k1w_first(int c, int NG) { return c == 0 ? 0 : 1 + c * NG; }
+__host__ __device__ constexpr int k1w_count(int c, int NG) { return c == 0 ? NG + 1 : NG; }
+
+__device__ __forceinline__ void k1w_issue(const float *f, float *dst, uint64_t *bar, int j, int nchunk, int NG,
+                                          int nx, int ny, size_t N) {
+    const int ri = j / nchunk, c = j - ri * nchunk;
+    const int yg = (int)blockIdx.x + ri * (int)gridDim.x;   // row over all runs
+    const int run = yg / ny, y = yg - run * ny;
+    const int i0 = k1w_first(c, NG), nf = k1w_count(c, NG);
+    const uint32_t rowbytes = (uint32_t)(nx * sizeof(float));
+    const float *fr = f + (size_t)run * Q * N;
+    mbar_expect_tx(bar, (uint32_t)nf * rowbytes);
+    for (int r = 0; r < nf; ++r)
+        bulk_g2s(dst + (size_t)r * nx, fr + (size_t)(i0 + r) * N + (size_t)y * nx, rowbytes, bar);
+}
+
 template <int H>
-__global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const float *__restrict__ f, float2 *spec, float *__restrict__ fields,
+__global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_wr(const float *__restrict__ f, float2 *spec, float *__restrict__ fields,
                                                  const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
                                                  KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = nt_wr<H>(), NWARP = NT / 32;
+    constexpr int NX = 2 * H, NT = nt_k1wr<H>(), NWARP = NT / 32;
     constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
     constexpr int NG = NWARP * RPW;                // row groups per block
     constexpr int CH = NG + 1, NCH = NMOV / NG;    // rows per chunk buffer, chunks per row
@@ -317,8 +353,8 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const floa
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
         mbar_init_fence();
-        if (njobs > 0) k1_issue(f, buf0, &bar0, 0, NCH, CH, nx, ny, N);
-        if (njobs > 1) k1_issue(f, buf1, &bar1, 1, NCH, CH, nx, ny, N);
+        if (njobs > 0) k1w_issue(f, buf0, &bar0, 0, NCH, NG, nx, ny, N);
+        if (njobs > 1) k1w_issue(f, buf1, &bar1, 1, NCH, NG, nx, ny, N);
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
@@ -336,7 +372,7 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const floa
         const int run = yg / ny, y = yg - run * ny;
         C *spec_r = spec + (size_t)run * NSLOT * slot;
         real *fields_r = fields + (size_t)run * 4 * N;
-        const int i0 = c * CH, nf = min(CH, Q - i0);
+        const int i0 = k1w_first(c, NG), nf = k1w_count(c, NG);
         if (!block_wait(bar, odd ? par1 : par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
             if (pend1) mbar_wait_bounded(&bar1, par1);
@@ -407,7 +443,7 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const floa
         fence_proxy_async();
         __syncthreads();
         if (tid == 0 && jb + 2 < njobs) {   // job jb + 2 reuses this buffer
-            k1_issue(f, B, bar, jb + 2, NCH, CH, nx, ny, N);
+            k1w_issue(f, B, bar, jb + 2, NCH, NG, nx, ny, N);
             if (odd) pend1 = true;
             else pend0 = true;
         }
@@ -417,7 +453,7 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k1_wr(const floa
 // shared memory of k1_wr<H>
 inline size_t k1_wr_smem(int H) {
     const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
-    const int CH = (nt_wr_host(H) / 32) * (32 / P) + 1;
+    const int CH = (nt_k1wr_host(H) / 32) * (32 / P) + 1;
     return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4,
                        (size_t)6 * 2 * H * 4});
 }
@@ -448,14 +484,14 @@ __device__ __forceinline__ void k3_issue(const typename cplx_of<real>::type *spe
 }
 
 template <int H>
-__global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *spec, const float *__restrict__ fields,
+__global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_wr(float2 *spec, const float *__restrict__ fields,
                                                  float *__restrict__ aux, const float2 *__restrict__ tw_g,
                                                  const float2 *__restrict__ Wp_g, const float *__restrict__ kxt,
                                                  KP<float> P, int *err) {
     using C = float2;
     using real = float;
-    constexpr int NX = 2 * H, NT = nt_wr<H>();
-    constexpr int PL = RowCfg<H>::P, RPW = 32 / PL;
+    constexpr int NX = 2 * H, NT = nt_k3wr<H>(), NB = nb_k3wr<H>();
+    constexpr int PL = RowCfg<H>::P, RPW = 32 / PL, NG = (NT / 32) * RPW;   // row groups
     constexpr int SMAX = (NX + NT - 1) / NT;
     constexpr int RB = ND1 + 2;   // rows per buffer
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -468,7 +504,7 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
     C *tw = (C *)sc.take(H * sizeof(C));
     C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
     real *buf0 = (real *)sc.take((size_t)RB * NX * sizeof(real));
-    real *buf1 = (real *)sc.take((size_t)RB * NX * sizeof(real));
+    real *buf1 = NB > 1 ? (real *)sc.take((size_t)RB * NX * sizeof(real)) : buf0;
     const int NY = P.nrun * ny;
     const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (tid == 0) {   // (the first copies start before the tables load)
@@ -476,15 +512,15 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
         mbar_init(&bar1, 1);
         mbar_init_fence();
         if (nrows > 0) k3_issue<real>(spec, fields, buf0, &bar0, 0, nx, ny, N, slot, H);
-        if (nrows > 1) k3_issue<real>(spec, fields, buf1, &bar1, 1, nx, ny, N, slot, H);
+        if (NB > 1 && nrows > 1) k3_issue<real>(spec, fields, buf1, &bar1, 1, nx, ny, N, slot, H);
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
     __syncthreads();
     uint32_t par0 = 0, par1 = 0;
-    bool pend0 = nrows > 0, pend1 = nrows > 1;
+    bool pend0 = nrows > 0, pend1 = NB > 1 && nrows > 1;
     for (int ri = 0; ri < nrows; ++ri) {
-        const bool odd = ri & 1;
+        const bool odd = NB > 1 && (ri & 1);
         uint64_t *bar = odd ? &bar1 : &bar0;
         const int yg = (int)blockIdx.x + ri * (int)gridDim.x;
         const int run = yg / ny, y = yg - run * ny;
@@ -505,8 +541,8 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
         real *d = odd ? buf1 : buf0;
         for (int k = tid; k < H; k += NT) k3_form_x<real>(reinterpret_cast<C *>(d), H, k, kxt[k], P.scale_x);
         __syncthreads();
-        if (grp < ND1) {
-            C *zr = reinterpret_cast<C *>(d) + (size_t)grp * H;
+        for (int r = grp; r < ND1; r += NG) {   // (uniform over each row group)
+            C *zr = reinterpret_cast<C *>(d) + (size_t)r * H;
             c2r_pre_wr<H>(zr, Wp, j);
             __syncwarp(group_mask<PL>());
             row_fft_wr<H, +1>(zr, tw, j, rsw);
@@ -547,17 +583,17 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
             d[4 * NX + x] = q2 * Ty;
         }
         __syncthreads();
-        if (grp < 5) {
-            C *zr = reinterpret_cast<C *>(d) + (size_t)grp * H;
+        for (int r = grp; r < 5; r += NG) {
+            C *zr = reinterpret_cast<C *>(d) + (size_t)r * H;
             row_fft_wr<H, -1>(zr, tw, j, rsw);
-            C *raw = k3_raw_slot(grp) >= 0 ? spec_r + (size_t)k3_raw_slot(grp) * slot + (size_t)y * H : nullptr;
-            C *mul = k3_mul_slot(grp) >= 0 ? spec_r + (size_t)k3_mul_slot(grp) * slot + (size_t)y * H : nullptr;
+            C *raw = k3_raw_slot(r) >= 0 ? spec_r + (size_t)k3_raw_slot(r) * slot + (size_t)y * H : nullptr;
+            C *mul = k3_mul_slot(r) >= 0 ? spec_r + (size_t)k3_mul_slot(r) * slot + (size_t)y * H : nullptr;
             r2c_post_wr2<H>(zr, raw, mul, kxt, P.scale_x, Wp, j);
         }
         fence_proxy_async();
         __syncthreads();
-        if (tid == 0 && ri + 2 < nrows) {
-            k3_issue<real>(spec, fields, d, bar, ri + 2, nx, ny, N, slot, H);
+        if (tid == 0 && ri + NB < nrows) {   // row ri + NB reuses this buffer
+            k3_issue<real>(spec, fields, d, bar, ri + NB, nx, ny, N, slot, H);
             if (odd) pend1 = true;
             else pend0 = true;
         }
@@ -567,7 +603,7 @@ __global__ void __launch_bounds__(nt_wr<H>(), H >= 256 ? 1 : 2) k3_wr(float2 *sp
 // shared memory of k3_wr<H>
 inline size_t k3_wr_smem(int H) {
     return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)(ND1 + 2) * 2 * H * 4,
-                       (size_t)(ND1 + 2) * 2 * H * 4});
+                       nb_k3wr_host(H) > 1 ? (size_t)(ND1 + 2) * 2 * H * 4 : 0});
 }
 
 // ---------------------------------------------------------------------------
