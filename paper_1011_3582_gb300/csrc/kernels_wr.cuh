@@ -349,15 +349,18 @@ __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_
     const int NY = P.nrun * ny;
     const int nrows = (int)blockIdx.x < NY ? (NY - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int njobs = nrows * NCH;
-    if (tid == 0) {   // (the first copies start before the tables load)
+    if (tid == 0) {   // (the first copies start while the tables load)
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
         mbar_init_fence();
+        grid_dep_wait();
         if (njobs > 0) k1w_issue(f, buf0, &bar0, 0, NCH, NG, nx, ny, N);
         if (njobs > 1) k1w_issue(f, buf1, &bar1, 1, NCH, NG, nx, ny, N);
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1;
@@ -511,11 +514,14 @@ __global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_
         mbar_init(&bar0, 1);
         mbar_init(&bar1, 1);
         mbar_init_fence();
+        grid_dep_wait();
         if (nrows > 0) k3_issue<real>(spec, fields, buf0, &bar0, 0, nx, ny, N, slot, H);
         if (NB > 1 && nrows > 1) k3_issue<real>(spec, fields, buf1, &bar1, 1, nx, ny, N, slot, H);
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
     uint32_t par0 = 0, par1 = 0;
     bool pend0 = nrows > 0, pend1 = NB > 1 && nrows > 1;
@@ -653,6 +659,7 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
         mbar_init(&hbar0, 1);
         mbar_init(&hbar1, 1);
         mbar_init_fence();
+        grid_dep_wait();
         if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, H);
         if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, H);
         if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, NCH, CH, nx, ny, slot, H);
@@ -660,6 +667,8 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
     uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
     bool pend0 = njobs > 0, pend1 = njobs > 1, hpend0 = nrows > 0, hpend1 = NHB > 1 && nrows > 1;
@@ -910,6 +919,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
         mbar_init(&bar1, 1);
         mbar_init(&abar, 1);
         mbar_init_fence();
+        grid_dep_wait();
         if (njobs > 0) kcol_issue(buf0, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
         if (nbuf > 1 && njobs > 1) kcol_issue(buf1, &bar1, groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
         if (njobs > nbuf) kcol_prefetch(groups, nbuf, ntiles, ngroups, TW, NY, BOXR, &tmap);
@@ -922,6 +932,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, ColCfg<NY>::TW
         gt[g] = ColG{G.nin, {G.in_slot[0], G.in_slot[1]}, G.out_slot[0], G.add_slot, (float)G.c[0][0][0],
                      (float)G.c[0][0][1]};
     }
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
     uint32_t par0 = 0, par1 = 0, apar = 0;
     bool pend0 = njobs > 0, pend1 = nbuf > 1 && njobs > 1;
@@ -1073,6 +1085,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
     if (tid == 0) {   // (the first copies start before the tables load)
         mbar_init(&bar0, 1);
         mbar_init_fence();
+        grid_dep_wait();
         if (njobs > 0) kcol_issue(in, &bar0, groups, 0, ntiles, ngroups, TW, NY, BOXR, &tmap);
         if (njobs > 1) kcol_prefetch(groups, 1, ntiles, ngroups, TW, NY, BOXR, &tmap);
     }
@@ -1085,6 +1098,8 @@ __global__ void __launch_bounds__(ColCfg<NY>::TW * ColCfg<NY>::P, 1) kcolm_wr(fl
         int *dst = reinterpret_cast<int *>(gs);
         for (int i = tid; i < nw; i += NT) dst[i] = src[i];
     }
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
     uint32_t par0 = 0;
     bool pend0 = njobs > 0;
