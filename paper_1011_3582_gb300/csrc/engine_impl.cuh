@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<re
                                                        const real *__restrict__ fields, double *partial,
                                                        const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                        const typename cplx_of<real>::type *__restrict__ Wp_g,
-                                                       KP<real> P, int with_grad) {
+                                                       const real *__restrict__ kxt, KP<real> P, int with_grad) {
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ double red[6][NT];
@@ -438,9 +438,14 @@ __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<re
     if (with_grad) {
         load_tables(Wr, Wr_g, h);
         load_tables(Wp, Wp_g, h);
-        for (int r = 0; r < 2; ++r) {
-            const C *src = spec + (size_t)(1 + r) * slot + (size_t)y * h;
-            for (int k = tid; k < h; k += NT) buf[(size_t)r * h + k] = src[k];
+        // row 0: D_x rho = i k_x rho^ / nx from the row spectrum in slot 0;
+        // row 1: D_y rho from the column pass (slot 2)
+        const C *r0 = spec + (size_t)y * h, *r2 = spec + 2 * slot + (size_t)y * h;
+        for (int k = tid; k < h; k += NT) {
+            const C z = r0[k];
+            const real m = kxt[k] * P.scale_x;
+            buf[k] = C{-m * z.y, m * z.x};
+            buf[(size_t)h + k] = r2[k];
         }
         rows_c2r(buf, h, 2, Wr, Wp);
         __syncthreads();
@@ -1240,11 +1245,12 @@ class EngineT : public Engine {
             add_out(g, 21 + 2 * i, 1, 0, DY);
             gs.push_back(g);
         }
-        // invariants: rho in slot 0 -> slots 1, 2
+        // invariants: rho in slot 0 -> D_y rho in slot 2 (one input, one
+        // output: the convection kernels; D_x rho is formed in the row
+        // spectrum by k_invariant_rows)
         inv_groups_ = (int)gs.size();
         {
             GroupDesc g = group(1, 0, 0);
-            add_out(g, 1, 1, 0, DX);
             add_out(g, 2, 1, 0, DY);
             gs.push_back(g);
         }
@@ -1657,14 +1663,6 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
-    Status run_groups(int first, int count, int nin_max) {
-        const size_t sm = nin_max == 1 ? smem_col1_ : smem_col2_;
-        k_col<real><<<dim3(h_ / TW_, count), NT, sm, stream_>>>(spec_, groups_ + first, kxt_, kyt_, Wc_, kp_, TW_,
-                                                                nin_max + 0);
-        FFTLB_LAUNCHED("k_col");
-        return Status::ok();
-    }
-
   public:
     Status enqueue_step() override {
         Status st;
@@ -1980,26 +1978,27 @@ class EngineT : public Engine {
         return Status::ok();
     }
 
+    // (one synchronisation: the sums and the device error word of the steps
+    // before them come back together)
     Status sums(bool with_grad, double out[6]) {
-        {
-            Status st = check_err();
-            if (!st.good()) return st;
-        }
         k_moments<real><<<grid1d(), 256, 0, stream_>>>(f0_, fields_, N_);
         FFTLB_LAUNCHED("k_moments");
         if (with_grad) {
             k_rows_forward<real, real><<<dim3(ny_, 1), NT, smem_rows1_, stream_>>>(fields_, spec_, 0, Wr_, Wp_, kp_);
             FFTLB_LAUNCHED("k_rows_forward");
-            Status st = run_groups(inv_groups_, 1, 1);
+            Status st = launch_col(inv_groups_, 1, false);
             if (!st.good()) return st;
         }
-        k_invariant_rows<real><<<ny_, NT, smem_inv_, stream_>>>(spec_, fields_, partial_, Wr_, Wp_, kp_,
+        k_invariant_rows<real><<<ny_, NT, smem_inv_, stream_>>>(spec_, fields_, partial_, Wr_, Wp_, kxt_, kp_,
                                                                 with_grad ? 1 : 0);
         FFTLB_LAUNCHED("k_invariant_rows");
         k_reduce_partials<<<1, NT, 0, stream_>>>(partial_, ny_, red_);
         FFTLB_LAUNCHED("k_reduce_partials");
+        int e = 0;
         FFTLB_CU(cudaMemcpyAsync(out, red_, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        FFTLB_CU(cudaMemcpyAsync(&e, err_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
         FFTLB_CU(cudaStreamSynchronize(stream_));
+        if (e) return Status::err(FFTLB_ERR_TIMEOUT, "a bounded device wait ran out (error word " + std::to_string(e) + ")");
         return Status::ok();
     }
 };
