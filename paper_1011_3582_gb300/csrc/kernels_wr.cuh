@@ -118,6 +118,12 @@ template <int H> __host__ __device__ constexpr int nhb_k5wr() { return nt_k5wr<H
 #define FFTLB_K5_UNROLL 4
 #endif
 constexpr int K5U = FFTLB_K5_UNROLL;
+// FFTLB_K5_VEC > 0: the epilogue with four consecutive sites per thread
+// (where nx is four times the block size) and 16-byte accesses (measured at
+// 1024^2: 130.9 us scalar, 126.7 us with 1, 131.9 us with 2)
+#ifndef FFTLB_K5_VEC
+#define FFTLB_K5_VEC 1
+#endif
 
 // position of stage-1 output (l, k1) in the row buffer.  P >= 16: k1 P +
 // (l ^ (k1 mod P)) (for P = 2E, k1 < E: k1 P + (l ^ k1)); P = 8: the row
@@ -299,6 +305,18 @@ __device__ __forceinline__ void c2r_pre_wr(C *z, const C *Wp, int j) {
             }
         }
     }
+}
+
+// four consecutive floats (16-byte aligned) to and from registers
+__device__ __forceinline__ void ld4(float (&a)[4], const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+}
+__device__ __forceinline__ void st4(float *p, const float (&a)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -781,6 +799,71 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
             const int v0 = 8 * k;
             const real sk = VX<real>(1 + v0), sk2 = V2<real>(1 + v0);
             const real *cres = B + (size_t)rr * 8 * NX;
+            if constexpr (NX == 4 * NT && FFTLB_K5_VEC > 0) {
+                // four consecutive sites per thread: 16-byte loads and stores
+                const int x0 = 4 * tid;
+                const size_t o0 = fo + (size_t)(1 + v0) * N + (size_t)y * nx + x0;
+                real rho[4], ux[4], uy[4], T[4], iT[4], e0[4], e1x[4], e1y[4], CC[4];
+                ld4(rho, Hd + 3 * nx + x0);
+                ld4(ux, Hd + 4 * nx + x0);
+                ld4(uy, Hd + 5 * nx + x0);
+                ld4(T, Hd + 6 * nx + x0);
+                ld4(iT, Hd + 8 * nx + x0);
+                ld4(e0, Hd + x0);
+                ld4(e1x, Hd + nx + x0);
+                ld4(e1y, Hd + 2 * nx + x0);
+                ld4(CC, Hd + 7 * nx + x0);
+                real rF[4], p0[4], p1[4], p2[4], p3[4], p4[4], g0[4], uxk[4], uyk[4], exk[4], eyk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const real qq = real(0.5) * (ux[q] * ux[q] + uy[q] * uy[q]) * iT[q], om = real(1) - qq;
+                    p0[q] = om + real(0.5) * qq * qq;
+                    p1[q] = om * iT[q];
+                    p2[q] = real(0.5) * om * iT[q] * iT[q];
+                    p3[q] = iT[q] * iT[q] * iT[q] * (real(1) / real(6));
+                    p4[q] = iT[q] * iT[q] * iT[q] * iT[q] * (real(1) / real(24));
+                    rF[q] = rho[q] * weight_Fk<real>(k, T[q]);   // Eq. 4
+                    g0[q] = e0[q] + CC[q] * sk2;
+                    uxk[q] = sk * ux[q];
+                    uyk[q] = sk * uy[q];
+                    exk[q] = sk * e1x[q];
+                    eyk[q] = sk * e1y[q];
+                }
+                // (FFTLB_K5_VEC = 1: the distributions of four directions are
+                // loaded before any of their stores, as fout may alias fcur or
+                // fbase; 2: all eight, through restrict-qualified pointers, as
+                // each element is read before the same thread writes it)
+                const real *__restrict__ pc = fcur + o0;
+                const real *__restrict__ pb = fbase + o0;
+                real *__restrict__ po = fout + o0;
+                constexpr int RH = FFTLB_K5_VEC == 1 ? 4 : 8;
+#pragma unroll
+                for (int r0 = 0; r0 < 8; r0 += RH) {
+                    real fc[RH][4], fb[RH][4];
+#pragma unroll
+                    for (int r = 0; r < RH; ++r) {
+                        ld4(fc[r], pc + (size_t)(r0 + r) * N);
+                        if (with_base) ld4(fb[r], pb + (size_t)(r0 + r) * N);
+                    }
+#pragma unroll
+                    for (int r = 0; r < RH; ++r) {
+                        real cv[4], fn[4];
+                        ld4(cv, cres + (size_t)(r0 + r) * NX + x0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const real vu = dir_dot<real>(r0 + r, uxk[q], uyk[q]);
+                            const real br = p0[q] + vu * (p1[q] + vu * (p2[q] + vu * (p3[q] + vu * p4[q])));
+                            const real fe = rF[q] * br;                                          // Eq. 3
+                            const real I = -(g0[q] + dir_dot<real>(r0 + r, exk[q], eyk[q])) * fe;  // Eq. 11
+                            const real rhs = -cv[q] - (fc[r][q] - fe) * itau + I;                // Eq. 10
+                            fn[q] = beta * (fc[r][q] + dt * rhs);
+                            if (with_base) fn[q] += alpha * fb[r][q];
+                        }
+                        st4(po + (size_t)(r0 + r) * N, fn);
+                    }
+                }
+                continue;
+            }
 #pragma unroll(K5U)
             for (int s = 0; s < SMAX; ++s) {
                 const int x = tid + s * NT;
