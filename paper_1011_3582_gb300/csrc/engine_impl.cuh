@@ -769,6 +769,7 @@ class EngineT : public Engine {
     std::vector<void *> allocs_;
     // group ranges in groups_
     int conv_groups_ = 0, l1_groups_ = 0, l2_groups_ = 0, grad_groups_ = 0, inv_groups_ = 0;
+    int nconv_ = NMOV;   // convection groups (velocities with v_y != 0)
     // warp-resident fp32 row kernels (kernels_wr.cuh) for nx = 512, 1024:
     // their stage-1 twiddle table and launch shape
     static constexpr bool wr_ok_ = std::is_same<real, float>::value && !SPLIT;
@@ -862,7 +863,7 @@ class EngineT : public Engine {
         // write once (one-sided spectra count N reals per field)
         const double alg[KK_COUNT] = {
             (33 + 38 + 4) * NN * s,                   // f in; 38 spectra + rho, u, T out
-            (32 + 32) * NN * s,                       // 32 spectra in, 32 out
+            2.0 * nconv_ * NN * s,                    // the v_y != 0 spectra in and out (24 + 24)
             (6 + 8) * NN * s,                         // 6 in, 8 out
             (14 + 2 + 3 + 6) * NN * s,                // 14 + rho, T in; 3 aux + 6 spectra out
             (3 + 3 + 3) * NN * s,                     // 3 in, 3 added, 3 out
@@ -1194,9 +1195,14 @@ class EngineT : public Engine {
         static const double DX[5] = {1, 0, 0, 0, 0}, DY[5] = {0, 1, 0, 0, 0};
         static const double DYY[5] = {0, 0, 0, -1, 0}, DXY[5] = {0, 0, 0, 0, -1};
         std::vector<GroupDesc> gs;
-        // convection: i (v_x k_x + v_y k_y) f_i, in place
+        // convection: i (v_x k_x + v_y k_y) f_i, in place, for the velocities
+        // with v_y != 0 (the row kernel K1 writes i v_x k_x f_i^ / nx for the
+        // others)
         conv_groups_ = (int)gs.size();
+        nconv_ = 0;
         for (int i = 1; i < Q; ++i) {
+            if (vy_[i] == 0.0) continue;
+            ++nconv_;
             GroupDesc g = group(1, i - 1, 0);
             const double c[5] = {vx_[i], vy_[i], 0, 0, 0};
             add_out(g, i - 1, 1, 0, c);
@@ -1897,26 +1903,26 @@ class EngineT : public Engine {
                 const int nt = nt_k1wr_host(h_);
                 auto *kern = h_ == 512 ? k1_wr<512> : h_ == 256 ? k1_wr<256> : k1_wr<128>;
                 if (!(st = launch_pdl("k1_wr", kern, grid1w_, nt, smem1w_, cur, specb_, fieldsb_,
-                                      (const float2 *)Tw1_, (const float2 *)Wp_, kp_, err_)).good())
+                                      (const float2 *)Tw1_, (const float2 *)Wp_, (const float *)kxt_, kp_, err_)).good())
                     return st;
                 k1done = true;
             }
         }
         if (k1done) {
         } else if (SMAX1_ == 1)
-            k1_pipe<real, 1, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 1, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kxt_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 2)
-            k1_pipe<real, 2, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_,
+            k1_pipe<real, 2, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kxt_, kp_,
                                                                                  CH1_, err_);
         else if (SMAX1_ == 4)
-            k1_pipe<real, 4, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
+            k1_pipe<real, 4, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kxt_, kp_, CH1_, err_);
         else
-            k1_pipe<real, 8, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kp_, CH1_, err_);
+            k1_pipe<real, 8, SPLIT><<<grid1_, NT1, smem1_, stream_>>>(cur, specb_, fieldsb_, Wr_, Wp_, Tr_, ntr_, kxt_, kp_, CH1_, err_);
         FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
-        if (!(st = launch_col(conv_groups_, NMOV, false)).good()) return st;
+        if (!(st = launch_col(conv_groups_, nconv_, false)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL1)).good()) return st;
         if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;

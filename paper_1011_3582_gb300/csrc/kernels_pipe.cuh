@@ -112,6 +112,10 @@ __device__ __forceinline__ void load_tab4(C *dst, const C *__restrict__ src, int
     }
 }
 
+// i m z
+template <typename real, typename C>
+__device__ __forceinline__ C imul(real m, C z) { return C{-m * z.y, m * z.x}; }
+
 // real value x of row r of a packed-complex row buffer in layout L
 template <typename real>
 __device__ __forceinline__ real real_at(const typename cplx_of<real>::type *buf, Lay L, int r, int x) {
@@ -162,7 +166,8 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
                                                              const typename cplx_of<real>::type *__restrict__ Wr_g,
                                                              const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                              const typename cplx_of<real>::type *__restrict__ Tr_g,
-                                                             int ntr, KP<real> P, int CH, int *err) {
+                                                             int ntr, const real *__restrict__ kxt, KP<real> P, int CH,
+                                                             int *err) {
     const uint4 *tc = TC ? P.tc16 : nullptr;   // split-BF16 tensor-core first passes
     using C = typename cplx_of<real>::type;
     constexpr int NT = KCfg<real, KS_K1>::NT;
@@ -248,8 +253,17 @@ __global__ void __launch_bounds__(KCfg<real, KS_K1>::NT, KCfg<real, KS_K1>::MINB
             r2c_post_l(res, lr, h, nf - r0, Wp, tid, NT);
             __syncthreads();
             for (int r = r0; r < nf; ++r) {
-                C *dst = spec_r + (size_t)(i0 + r - 1) * slot + (size_t)y * h;
-                for (int k = tid; k < h; k += NT) dst[k] = res[lr(r - r0, k)];
+                const int i = i0 + r;
+                C *dst = spec_r + (size_t)(i - 1) * slot + (size_t)y * h;
+                if (VY<real>(i) == real(0)) {
+                    // v_y = 0: the convection term needs no column pass; its
+                    // row spectrum is i v_x k_x f^ / nx (the 1 / nx the column
+                    // pass would leave)
+                    const real sx = VX<real>(i) * P.scale_x;
+                    for (int k = tid; k < h; k += NT) dst[k] = imul(kxt[k] * sx, res[lr(r - r0, k)]);
+                } else {
+                    for (int k = tid; k < h; k += NT) dst[k] = res[lr(r - r0, k)];
+                }
             }
         }
         if (c == nchunk - 1) {
@@ -684,10 +698,6 @@ __global__ void __launch_bounds__(KCfg<real, KS_COL>::NT, KCfg<real, KS_COL>::MI
 // ---------------------------------------------------------------------------
 
 constexpr int NT3 = 256;
-
-// i m z
-template <typename real, typename C>
-__device__ __forceinline__ C imul(real m, C z) { return C{-m * z.y, m * z.x}; }
 
 // The level-1 derivatives K3 forms in the row spectrum (k3_src_slot), at
 // bin k of the one-sided rows of d (row o at d + o rs; bin 0 carries DC and

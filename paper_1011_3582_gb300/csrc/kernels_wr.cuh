@@ -350,7 +350,7 @@ __device__ __forceinline__ void k1w_issue(const float *f, float *dst, uint64_t *
 template <int H>
 __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_wr(const float *__restrict__ f, float2 *spec, float *__restrict__ fields,
                                                  const float2 *__restrict__ tw_g, const float2 *__restrict__ Wp_g,
-                                                 KP<float> P, int *err) {
+                                                 const float *__restrict__ kxt, KP<float> P, int *err) {
     using C = float2;
     using real = float;
     constexpr int NX = 2 * H, NT = nt_k1wr<H>(), NWARP = NT / 32;
@@ -436,9 +436,14 @@ __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_
         {
             const int r = grp + (c == 0 ? 1 : 0);
             if (r < nf) {
+                const int i = i0 + r;
                 C *zr = reinterpret_cast<C *>(B) + (size_t)r * H;
+                C *dst = spec_r + (size_t)(i - 1) * slot + (size_t)y * H;
                 row_fft_wr<H, -1>(zr, tw, j, rsw);
-                r2c_post_wr<H>(zr, spec_r + (size_t)(i0 + r - 1) * slot + (size_t)y * H, Wp, j);
+                if (VY<real>(i) == real(0))   // convection in k_x alone: i v_x k_x f^ / nx, no column pass
+                    r2c_post_wr2<H>(zr, (C *)nullptr, dst, kxt, VX<real>(i) * P.scale_x, Wp, j);
+                else
+                    r2c_post_wr<H>(zr, dst, Wp, j);
             }
         }
         if (c == NCH - 1) {

@@ -5,7 +5,9 @@ k_y (Eqs. K1-K4), so a derivative in k_x alone needs no column transform:
 the stage's level-1 column pass forms only the 8 outputs that involve k_y,
 the row kernel K3 forms the other 7 in the row spectrum (k3_form_x in
 kernels_pipe.cuh) and, for level 2, writes i k_x X / nx of Lambda_xx,
-Lambda_xy, Phi_x for the column pass to add to its d_y terms.  This test
+Lambda_xy, Phi_x for the column pass to add to its d_y terms; the
+convection terms of the velocities with v_y = 0 skip the column pass the
+same way.  This test
 runs that data flow with numpy in the engine's layouts (one-sided row
 spectra with the row-Nyquist value packed into bin 0, unnormalised column
 transforms with the 1 / (nx ny) multiplier scale, unnormalised inverse rows)
@@ -116,6 +118,27 @@ def test_split_derivatives_match_composed_D(ny, nx, window):
     for k, Z in out.items():
         got = row_inv(Z)
         assert np.abs(got - want2[k]).max() < 1e-9 * max(1.0, np.abs(want2[k]).max()), k
+
+
+@pytest.mark.parametrize("ring_speed", [1.0, 2.7])
+def test_convection_without_v_y_needs_no_column_pass(ring_speed):
+    """Directions 0 and 4 of every ring have v_y = 0 (Eq. 1): the column pass
+    of i (v_x k_x + v_y k_y) X leaves i v_x k_x X / nx, the form the row
+    kernel K1 writes for them (k1_wr, k1_pipe); against the oracle's
+    v_x D_x f as well."""
+    ny, nx, window, dx = 16, 32, 4, 1.0 / 64
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal((ny, nx))
+    h = nx // 2
+    kx = np.array([kappa_engine(j, nx, dx, window) for j in range(h + 1)])
+    ky = np.array([kappa_engine(j if j < ny // 2 else j - ny, ny, dx, window) for j in range(ny)])
+    S = row_spec(f)
+    for vx in (ring_speed, -ring_speed):
+        col = col_pass([((vx, 0, 0, 0, 0), S)], kx, ky, 1.0 / (nx * ny))
+        k1 = 1j * (vx * kx[None, :h] / nx) * S
+        assert np.abs(col - k1).max() < 1e-12 * np.abs(col).max()
+        want = vx * O.D(f, 'x', dx, window)
+        assert np.abs(row_inv(k1) - want).max() < 1e-9 * np.abs(want).max()
 
 
 def test_planted_mistake_is_caught():
