@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_
     SmemCursor sc{smem_raw, 0u};
     C *tw = (C *)sc.take(H * sizeof(C));
     C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
+    real *kxs = (real *)sc.take(H * sizeof(real));   // k_x of the row bins
     real *buf0 = (real *)sc.take((size_t)CH * NX * sizeof(real));
     real *buf1 = (real *)sc.take((size_t)CH * NX * sizeof(real));
     real *fb = (real *)sc.take((size_t)6 * NX * sizeof(real));   // rho, ux, uy, T, Pi, g rows
@@ -384,6 +385,7 @@ __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    load_tab4(kxs, kxt, H, NT);
     grid_dep_wait();
     grid_dep_launch();
     __syncthreads();
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_
                 C *dst = spec_r + (size_t)(i - 1) * slot + (size_t)y * H;
                 row_fft_wr<H, -1>(zr, tw, j, rsw);
                 if (VY<real>(i) == real(0))   // convection in k_x alone: i v_x k_x f^ / nx, no column pass
-                    r2c_post_wr2<H>(zr, (C *)nullptr, dst, kxt, VX<real>(i) * P.scale_x, Wp, j);
+                    r2c_post_wr2<H>(zr, (C *)nullptr, dst, kxs, VX<real>(i) * P.scale_x, Wp, j);
                 else
                     r2c_post_wr<H>(zr, dst, Wp, j);
             }
@@ -487,8 +489,8 @@ __global__ void __launch_bounds__(nt_k1wr<H>(), nt_k1wr<H>() >= 512 ? 1 : 2) k1_
 inline size_t k1_wr_smem(int H) {
     const int P = H == 512 ? 32 : H == 256 ? 16 : 8;
     const int CH = (nt_k1wr_host(H) / 32) * (32 / P) + 1;
-    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)CH * 2 * H * 4, (size_t)CH * 2 * H * 4,
-                       (size_t)6 * 2 * H * 4});
+    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)H * 4, (size_t)CH * 2 * H * 4,
+                       (size_t)CH * 2 * H * 4, (size_t)6 * 2 * H * 4});
 }
 
 // ---------------------------------------------------------------------------
@@ -536,6 +538,7 @@ __global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_
     SmemCursor sc{smem_raw, 0u};
     C *tw = (C *)sc.take(H * sizeof(C));
     C *Wp = (C *)sc.take((H / 2 + 1) * sizeof(C));
+    real *kxs = (real *)sc.take(H * sizeof(real));   // k_x of the row bins
     real *buf0 = (real *)sc.take((size_t)RB * NX * sizeof(real));
     real *buf1 = NB > 1 ? (real *)sc.take((size_t)RB * NX * sizeof(real)) : buf0;
     const int NY = P.nrun * ny;
@@ -550,6 +553,7 @@ __global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
+    load_tab4(kxs, kxt, H, NT);
     grid_dep_wait();
     grid_dep_launch();
     __syncthreads();
@@ -575,7 +579,7 @@ __global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_
             pend0 = false;
         }
         real *d = odd ? buf1 : buf0;
-        for (int k = tid; k < H; k += NT) k3_form_x<real>(reinterpret_cast<C *>(d), H, k, kxt[k], P.scale_x);
+        for (int k = tid; k < H; k += NT) k3_form_x<real>(reinterpret_cast<C *>(d), H, k, kxs[k], P.scale_x);
         __syncthreads();
         for (int r = grp; r < ND1; r += NG) {   // (uniform over each row group)
             C *zr = reinterpret_cast<C *>(d) + (size_t)r * H;
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_
             row_fft_wr<H, -1>(zr, tw, j, rsw);
             C *raw = k3_raw_slot(r) >= 0 ? spec_r + (size_t)k3_raw_slot(r) * slot + (size_t)y * H : nullptr;
             C *mul = k3_mul_slot(r) >= 0 ? spec_r + (size_t)k3_mul_slot(r) * slot + (size_t)y * H : nullptr;
-            r2c_post_wr2<H>(zr, raw, mul, kxt, P.scale_x, Wp, j);
+            r2c_post_wr2<H>(zr, raw, mul, kxs, P.scale_x, Wp, j);
         }
         fence_proxy_async();
         __syncthreads();
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(nt_k3wr<H>(), nt_k3wr<H>() >= 512 ? 1 : 2) k3_
 
 // shared memory of k3_wr<H>
 inline size_t k3_wr_smem(int H) {
-    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)(ND1 + 2) * 2 * H * 4,
+    return smem_bytes({(size_t)H * 8, (size_t)(H / 2 + 1) * 8, (size_t)H * 4, (size_t)(ND1 + 2) * 2 * H * 4,
                        nb_k3wr_host(H) > 1 ? (size_t)(ND1 + 2) * 2 * H * 4 : 0});
 }
 
@@ -763,6 +767,50 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
             // per-site coefficients over the head rows (same site, same
             // thread): row 0 <- e0, 1 <- e1x, 2 <- e1y, 7 <- C + C_q, 8 <- 1/T;
             // the rest velocity's update
+            if constexpr (NX == 4 * NT && FFTLB_K5_VEC > 0) {   // four consecutive sites per thread
+                const int x0 = 4 * tid;
+                const size_t o = fo + (size_t)y * nx + x0;
+                real rho[4], ux[4], uy[4], T[4], dLx[4], dLy[4], dPh[4], a7[4], a8[4], a9[4], fc[4], fb[4];
+                ld4(rho, Hd + 3 * nx + x0);
+                ld4(ux, Hd + 4 * nx + x0);
+                ld4(uy, Hd + 5 * nx + x0);
+                ld4(T, Hd + 6 * nx + x0);
+                ld4(dLx, Hd + x0);
+                ld4(dLy, Hd + nx + x0);
+                ld4(dPh, Hd + 2 * nx + x0);
+                ld4(a7, Hd + 7 * nx + x0);
+                ld4(a8, Hd + 8 * nx + x0);
+                ld4(a9, Hd + 9 * nx + x0);
+                ld4(fc, fcur + o);
+                if (with_base) ld4(fb, fbase + o);
+                real e0[4], e1x[4], e1y[4], CC[4], iT[4], fn[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const real rT = rho[q] * T[q];
+                    const real inv2 = real(1) / (real(2) * rho[q] * T[q] * T[q]);
+                    const real Bx = (a8[q] + dLx[q]) / rT;      // Eq. 21
+                    const real By = (a9[q] + dLy[q]) / rT;
+                    CC[q] = (a7[q] + dPh[q]) * inv2;            // C + C_q, Eqs. 22-23
+                    const real A = real(-2) * CC[q] * T[q];      // Eq. 20
+                    const real u2 = ux[q] * ux[q] + uy[q] * uy[q];
+                    e0[q] = A - (Bx * ux[q] + By * uy[q]) + CC[q] * u2;
+                    e1x[q] = Bx - real(2) * CC[q] * ux[q];
+                    e1y[q] = By - real(2) * CC[q] * uy[q];
+                    iT[q] = real(1) / T[q];
+                    real F[5];
+                    weights_Fk<real>(T[q], F);
+                    const real qq = real(0.5) * u2 / T[q], om = real(1) - qq;
+                    const real fe = rho[q] * F[0] * (om + real(0.5) * qq * qq);
+                    fn[q] = beta * (fc[q] + dt * (-(fc[q] - fe) * itau - e0[q] * fe));
+                    if (with_base) fn[q] += alpha * fb[q];
+                }
+                st4(Hd + x0, e0);
+                st4(Hd + nx + x0, e1x);
+                st4(Hd + 2 * nx + x0, e1y);
+                st4(Hd + 7 * nx + x0, CC);
+                st4(Hd + 8 * nx + x0, iT);
+                st4(fout + o, fn);
+            } else
 #pragma unroll 1
             for (int s = 0; s < SMAX; ++s) {
                 const int x = tid + s * NT;
