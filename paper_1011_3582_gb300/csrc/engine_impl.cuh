@@ -770,6 +770,7 @@ class EngineT : public Engine {
     // group ranges in groups_
     int conv_groups_ = 0, l1_groups_ = 0, l2_groups_ = 0, grad_groups_ = 0, inv_groups_ = 0;
     int nconv_ = NMOV;   // convection groups (velocities with v_y != 0)
+    int nconvl_ = NMOV;  // ... and the one-input level-1 groups after them
     // warp-resident fp32 row kernels (kernels_wr.cuh) for nx = 512, 1024:
     // their stage-1 twiddle table and launch shape
     static constexpr bool wr_ok_ = std::is_same<real, float>::value && !SPLIT;
@@ -863,8 +864,8 @@ class EngineT : public Engine {
         // write once (one-sided spectra count N reals per field)
         const double alg[KK_COUNT] = {
             (33 + 38 + 4) * NN * s,                   // f in; 38 spectra + rho, u, T out
-            2.0 * nconv_ * NN * s,                    // the v_y != 0 spectra in and out (24 + 24)
-            (6 + 8) * NN * s,                         // 6 in, 8 out
+            2.0 * nconvl_ * NN * s,                   // the v_y != 0 spectra and T, Pi, g in; as many out
+            (3 + 5) * NN * s,                         // rho, u_x, u_y in; 5 out
             (14 + 2 + 3 + 6) * NN * s,                // 14 + rho, T in; 3 aux + 6 spectra out
             (3 + 3 + 3) * NN * s,                     // 3 in, 3 added, 3 out
             (32 + 3 + 4 + 3 + 33 + 33 * fbase + 33) * NN * s};
@@ -1208,7 +1209,19 @@ class EngineT : public Engine {
             add_out(g, i - 1, 1, 0, c);
             gs.push_back(g);
         }
-        // level 1: the outputs that involve k_y (k3_src_slot: K3 forms the rest)
+        // level 1: the outputs that involve k_y (k3_src_slot: K3 forms the
+        // rest).  The three of one input and one output (d_y T, d_y Pi, d_y g)
+        // run with the convection groups, in the same launch (nconvl_ groups
+        // from conv_groups_); rho and u run as the level-1 launch.
+        {
+            const int singles[3][2] = {{SLOT_T, D_TY}, {SLOT_PI, D_PIY}, {SLOT_G, D_GY}};
+            for (auto &sgl : singles) {
+                GroupDesc g = group(1, sgl[0], 0);
+                add_out(g, SLOT_D1 + sgl[1], 1, 0, DY);
+                gs.push_back(g);
+            }
+            nconvl_ = nconv_ + 3;
+        }
         l1_groups_ = (int)gs.size();
         {
             GroupDesc g = group(1, SLOT_RHO, 0);
@@ -1221,12 +1234,6 @@ class EngineT : public Engine {
             add_out(g, SLOT_D1 + D_UXY, 1, 0, DY);
             add_out(g, SLOT_D1 + D_UYY, 1, 1, DY);
             add_out(g, SLOT_D1 + D_DIVY, 2, 0, DXY, 1, DYY);   // D_y (D_x u_x + D_y u_y)
-            gs.push_back(g);
-        }
-        const int singles[3][2] = {{SLOT_T, D_TY}, {SLOT_PI, D_PIY}, {SLOT_G, D_GY}};
-        for (auto &sgl : singles) {
-            GroupDesc g = group(1, sgl[0], 0);
-            add_out(g, SLOT_D1 + sgl[1], 1, 0, DY);
             gs.push_back(g);
         }
         // level 2: d_y of Lambda_xy, Lambda_yy, Phi_y plus the d_x terms K3
@@ -1922,10 +1929,10 @@ class EngineT : public Engine {
         FFTLB_LAUNCHED("k1_pipe");
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_CONV)).good()) return st;
-        if (!(st = launch_col(conv_groups_, nconv_, false)).good()) return st;
+        if (!(st = launch_col(conv_groups_, nconvl_, false)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_COL_LEVEL1)).good()) return st;
-        if (!(st = launch_col(l1_groups_, 5, true)).good()) return st;
+        if (!(st = launch_col(l1_groups_, 2, true)).good()) return st;
         if (!(st = prof_end()).good()) return st;
         if (!(st = prof_begin(KK_ROW_LEVEL1)).good()) return st;
         bool k3done = false;
