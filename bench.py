@@ -107,8 +107,9 @@ def write_ncu_traffic(csv_path, precision, n, note, out_path=None):
     """Writes profiles/ncu_traffic.txt from an ncu --csv log of one SSP-RK3
     step of the pipelined kernels captured with the metrics
     dram__bytes_read.sum and dram__bytes_write.sum: DRAM bytes per launch of
-    each kernel kind, averaged over its launches (the two multi-group column
-    launches of a stage alternate: level 1, then level 2)."""
+    each kernel kind, averaged over its launches (the one-input column
+    launches of a stage alternate: convection, then level 2; the multi-input
+    column launch is level 1)."""
     import csv
     rows = [ln for ln in open(csv_path) if ln.startswith('"')]
     per = {}
@@ -117,7 +118,7 @@ def write_ncu_traffic(csv_path, precision, n, note, out_path=None):
             continue
         by = float(r["Metric Value"].replace(",", "")) * _UNITS.get(r["Metric Unit"], 1.0)
         per.setdefault(int(r["ID"]), [r["Kernel Name"], 0.0])[1] += by
-    out, multi = {}, 0
+    out, single = {}, 0
     for i in sorted(per):
         name, by = per[i]
         if "k1_pipe" in name or "k1_wr" in name:
@@ -126,15 +127,15 @@ def write_ncu_traffic(csv_path, precision, n, note, out_path=None):
             k = "row_level1"
         elif "k5_pipe" in name or "k5_wr" in name:
             k = "row_final"
-        elif "kcol_wr" in name:
-            k = "col_convection"
-        elif "kcol_pipe" in name or "kcolm_wr" in name:
+        elif "kcolm_wr" in name:
+            k = "col_level1"
+        elif "kcol_wr" in name or "kcol_pipe" in name:
             m = re.search(r"kcol_pipe<\s*\w+\s*,\s*(\w+)", name)   # the second template argument: MULTI
-            if m and m.group(1) in ("false", "0"):
-                k = "col_convection"
+            if m and m.group(1) not in ("false", "0"):
+                k = "col_level1"
             else:
-                k = "col_level1" if multi % 2 == 0 else "col_level2"
-                multi += 1
+                k = "col_convection" if single % 2 == 0 else "col_level2"
+                single += 1
         else:
             continue
         out.setdefault(k, []).append(by)

@@ -110,15 +110,22 @@ def test_reference_arm_does_no_work_on_other_ranks(capsys):
 
 def test_ncu_traffic_summary_from_a_launch_csv(tmp_path):
     """bench.write_ncu_traffic: DRAM read + write per launch, unit-scaled,
-    averaged per kernel kind; the two multi-group column launches of a stage
-    alternate between level 1 and level 2."""
+    averaged per kernel kind; the one-input column launches of a stage
+    alternate between convection and level 2, the multi-input one is level
+    1 (both the pipelined and the warp-resident kernel names)."""
     sys.path.insert(0, ROOT)
     import bench
     hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
           '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
-    names = ["void k1_pipe<float, 4, false>(x)", "void kcol_pipe<float, false, false>(x)",
-             "void kcol_pipe<float, true, false>(x)", "void k3_pipe<float, false>(x)",
-             "void kcol_pipe<float, true, false>(x)", "void k5_pipe<float, 2, false>(x)"]
+    for names in (["void k1_pipe<float, 4, false>(x)", "void kcol_pipe<float, false, false>(x)",
+                   "void kcol_pipe<float, true, false>(x)", "void k3_pipe<float, false>(x)",
+                   "void kcol_pipe<float, false, false>(x)", "void k5_pipe<float, 2, false>(x)"],
+                  ["void k1_wr<512>(x)", "void kcol_wr<1024>(x)", "void kcolm_wr<1024>(x)", "void k3_wr<512>(x)",
+                   "void kcol_wr<1024>(x)", "void k5_wr<512>(x)"]):
+        _check_traffic_names(tmp_path, bench, hdr, names)
+
+
+def _check_traffic_names(tmp_path, bench, hdr, names):
     lines = ["==PROF== noise\n", hdr]
     for stage in range(2):
         for j, nm in enumerate(names):
