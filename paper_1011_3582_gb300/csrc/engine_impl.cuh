@@ -1839,9 +1839,20 @@ class EngineT : public Engine {
 #ifndef FFTLB_PDL
 #define FFTLB_PDL 0
 #endif
+    // The final row kernel alone (FFTLB_PDL_K5): it overlaps the level-2
+    // launch's tail with its first convection chunk, and only its head copies
+    // wait for that launch.
+#ifndef FFTLB_PDL_K5
+#define FFTLB_PDL_K5 0
+#endif
     template <typename... KArgs, typename... Args>
     Status launch_pdl(const char *name, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
                       Args &&...args) {
+        return launch_ex(name, FFTLB_PDL, kernel, grid, block, smem, std::forward<Args>(args)...);
+    }
+    template <typename... KArgs, typename... Args>
+    Status launch_ex(const char *name, int pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                     Args &&...args) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(block);
@@ -1849,7 +1860,7 @@ class EngineT : public Engine {
         cfg.stream = stream_;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = FFTLB_PDL;
+        at[0].val.programmaticStreamSerializationAllowed = pdl;
         cfg.attrs = at;
         cfg.numAttrs = 1;
         const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
@@ -1961,7 +1972,7 @@ class EngineT : public Engine {
             if (k5wr_) {
                 const int nt = nt_k5wr_host(h_);
                 auto *kern = h_ == 512 ? k5_wr<512> : h_ == 256 ? k5_wr<256> : k5_wr<128>;
-                if (!(st = launch_pdl("k5_wr", kern, grid5w_, nt, smem5w_, (const float2 *)specb_,
+                if (!(st = launch_ex("k5_wr", FFTLB_PDL || FFTLB_PDL_K5, kern, grid5w_, nt, smem5w_, (const float2 *)specb_,
                                       (const float *)fieldsb_, (const float *)auxb_, cur, base, out, alpha, beta,
                                       (const float2 *)Tw1_, (const float2 *)Wp_, kp_, err_)).good())
                     return st;

@@ -693,15 +693,19 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
         mbar_init(&hbar0, 1);
         mbar_init(&hbar1, 1);
         mbar_init_fence();
+        // Only the head's level-2 rows come from the launch just before this
+        // one (the level-2 columns); the convection spectra, fields, aux rows
+        // and distributions were complete before that launch began, and that
+        // launch touches none of what this kernel writes.  So under a
+        // programmatic dependent launch only the head copies wait.
+        if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, NCH, CH, nx, ny, slot, H);
+        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, NCH, CH, nx, ny, slot, H);
         grid_dep_wait();
         if (nrows > 0) k5_issue_head<real>(spec, fields, aux, head0, &hbar0, 0, nx, ny, N, slot, H);
         if (NHB > 1 && nrows > 1) k5_issue_head<real>(spec, fields, aux, head1, &hbar1, 1, nx, ny, N, slot, H);
-        if (njobs > 0) k5_issue_chunk<real>(spec, buf0, &bar0, 0, NCH, CH, nx, ny, slot, H);
-        if (njobs > 1) k5_issue_chunk<real>(spec, buf1, &bar1, 1, NCH, CH, nx, ny, slot, H);
     }
     load_tab4(tw, tw_g, H, NT);
     load_tab4(Wp, Wp_g, H / 2 + 1, NT);
-    grid_dep_wait();
     grid_dep_launch();
     __syncthreads();
     uint32_t par0 = 0, par1 = 0, hpar0 = 0, hpar1 = 0;
@@ -716,22 +720,6 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
         const int run = yg / ny, y = yg - run * ny;
         const size_t fo = (size_t)run * Q * N;
         real *Hd = hodd ? head1 : head0;
-        if (c == 0) {
-            if (!block_wait(hodd ? &hbar1 : &hbar0, hodd ? hpar1 : hpar0, err)) {
-                if (pend0) mbar_wait_bounded(&bar0, par0);
-                if (pend1) mbar_wait_bounded(&bar1, par1);
-                if (hpend0) mbar_wait_bounded(&hbar0, hpar0);
-                if (hpend1) mbar_wait_bounded(&hbar1, hpar1);
-                return;
-            }
-            if (hodd) {
-                hpar1 ^= 1;
-                hpend1 = false;
-            } else {
-                hpar0 ^= 1;
-                hpend0 = false;
-            }
-        }
         if (!block_wait(odd ? &bar1 : &bar0, odd ? par1 : par0, err)) {
             if (pend0) mbar_wait_bounded(&bar0, par0);
             if (pend1) mbar_wait_bounded(&bar1, par1);
@@ -748,18 +736,35 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
         }
         real *B = odd ? buf1 : buf0;
         // inverse transforms: convection row grow of the chunk; with the
-        // first chunk, the 3 level-2 rows of the head (row groups 0..2)
+        // first chunk, then (its copies complete) the 3 level-2 rows of the
+        // head (row groups 0..2)
         {
             const unsigned gm = group_mask<PL>();
             C *zr = reinterpret_cast<C *>(B) + (size_t)grow * H;
             c2r_pre_wr<H>(zr, Wp, j);
             __syncwarp(gm);
             row_fft_wr<H, +1>(zr, tw, j, rsw);
-            if (c == 0 && grow < 3) {   // uniform over each row group
-                C *zh = reinterpret_cast<C *>(Hd) + (size_t)grow * H;
-                c2r_pre_wr<H>(zh, Wp, j);
-                __syncwarp(gm);
-                row_fft_wr<H, +1>(zh, tw, j, rsw);
+            if (c == 0) {
+                if (!block_wait(hodd ? &hbar1 : &hbar0, hodd ? hpar1 : hpar0, err)) {
+                    if (pend0) mbar_wait_bounded(&bar0, par0);
+                    if (pend1) mbar_wait_bounded(&bar1, par1);
+                    if (hpend0) mbar_wait_bounded(&hbar0, hpar0);
+                    if (hpend1) mbar_wait_bounded(&hbar1, hpar1);
+                    return;
+                }
+                if (hodd) {
+                    hpar1 ^= 1;
+                    hpend1 = false;
+                } else {
+                    hpar0 ^= 1;
+                    hpend0 = false;
+                }
+                if (grow < 3) {   // uniform over each row group
+                    C *zh = reinterpret_cast<C *>(Hd) + (size_t)grow * H;
+                    c2r_pre_wr<H>(zh, Wp, j);
+                    __syncwarp(gm);
+                    row_fft_wr<H, +1>(zh, tw, j, rsw);
+                }
             }
         }
         __syncthreads();
