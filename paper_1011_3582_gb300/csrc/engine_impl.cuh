@@ -864,8 +864,8 @@ class EngineT : public Engine {
         // write once (one-sided spectra count N reals per field)
         const double alg[KK_COUNT] = {
             (33 + 38 + 4) * NN * s,                   // f in; 38 spectra + rho, u, T out
-            2.0 * nconvl_ * NN * s,                   // the v_y != 0 spectra and T, Pi, g in; as many out
-            (3 + 5) * NN * s,                         // rho, u_x, u_y in; 5 out
+            2.0 * nconvl_ * NN * s,                   // the v_y != 0 spectra and T, Pi, g, u_y in; as many out
+            (3 + 4) * NN * s,                         // rho, u_x, u_y in; 4 out
             (14 + 2 + 3 + 6) * NN * s,                // 14 + rho, T in; 3 aux + 6 spectra out
             (3 + 3 + 3) * NN * s,                     // 3 in, 3 added, 3 out
             (32 + 3 + 4 + 3 + 33 + 33 * fbase + 33) * NN * s};
@@ -1210,17 +1210,19 @@ class EngineT : public Engine {
             gs.push_back(g);
         }
         // level 1: the outputs that involve k_y (k3_src_slot: K3 forms the
-        // rest).  The three of one input and one output (d_y T, d_y Pi, d_y g)
-        // run with the convection groups, in the same launch (nconvl_ groups
-        // from conv_groups_); rho and u run as the level-1 launch.
+        // rest).  Four of one input and one output (d_y T, d_y Pi, d_y g,
+        // d_y u_y) run with the convection groups, in the same launch
+        // (nconvl_ groups from conv_groups_: they fill its last round of
+        // jobs); rho (d_y, d_yy) and u (d_y u_x, d_y div u) run as the
+        // level-1 launch.
         {
-            const int singles[3][2] = {{SLOT_T, D_TY}, {SLOT_PI, D_PIY}, {SLOT_G, D_GY}};
+            const int singles[4][2] = {{SLOT_T, D_TY}, {SLOT_PI, D_PIY}, {SLOT_G, D_GY}, {SLOT_UY, D_UYY}};
             for (auto &sgl : singles) {
                 GroupDesc g = group(1, sgl[0], 0);
                 add_out(g, SLOT_D1 + sgl[1], 1, 0, DY);
                 gs.push_back(g);
             }
-            nconvl_ = nconv_ + 3;
+            nconvl_ = nconv_ + 4;
         }
         l1_groups_ = (int)gs.size();
         {
@@ -1232,7 +1234,6 @@ class EngineT : public Engine {
         {
             GroupDesc g = group(2, SLOT_UX, SLOT_UY);
             add_out(g, SLOT_D1 + D_UXY, 1, 0, DY);
-            add_out(g, SLOT_D1 + D_UYY, 1, 1, DY);
             add_out(g, SLOT_D1 + D_DIVY, 2, 0, DXY, 1, DYY);   // D_y (D_x u_x + D_y u_y)
             gs.push_back(g);
         }
