@@ -9,7 +9,8 @@ Reading (time step): the paper's dt = 1e-5 needs millions of steps to reach
 equilibrium (t = 20-30).  These runs use dt = 1e-4, inside the stability
 limits of SSP-RK3 (dt |v|max k_max = 0.28 for the window-4 symbol at
 dx = 1/256, dt / tau = 0.01), and the coexistence experiment repeats the
-fp32 runs at dt = 5e-5 to show the averaged densities do not depend on it.
+runs at dt = 5e-5 (fp64 and fp32) to show the averaged densities do not
+depend on it.
 Bulk values are averaged over the second half of each run, because the
 acoustic oscillations the initial profiles launch decay only on the
 viscous time L^2 / nu (see paper_1011_3582_gb300.physics).
@@ -145,6 +146,31 @@ def test_coexistence_fp32(fl):
             print("  a=%.4f T0=%.4f: dt/2 - dt rho_v %+.2e rho_l %+.2e"
                   % (x["a"], x["T0"], (y["rho_v"] - x["rho_v"]) / x["rho_v"], (y["rho_l"] - x["rho_l"]) / x["rho_l"]))
     assert all(r["finite"] for r in a + b)
+
+
+@LONG
+def test_coexistence_fp64_half_dt(fl):
+    """The time-step reading: the paper's fluid at the six quench temperatures
+    0.87 .. 0.97 in fp64 at dt = 1e-4 and at dt = 5e-5, both to t = 4, bulk
+    densities averaged over t in [2, 4].  A stationary state L(f) = 0 is a
+    fixed point of SSP-RK3 for every dt; the relaxing runs differ only by the
+    time-integration error of the transient (third order in dt), which the
+    averaged densities must show below 1e-4."""
+    COEXP = [(9 / 8, 1 / 3, T) for T in (0.87, 0.89, 0.91, 0.93, 0.95, 0.97)]
+    out = {}
+    for dt in (1e-4, 5e-5):
+        runs = [slab_run(fl, a, b, T, 64, dt) for a, b, T in COEXP]
+        out[dt] = PH.relax(fl, runs, t_end=4.0, sample_dt=0.1)
+    rows = []
+    for (a, b, T0), x, y in zip(COEXP, out[1e-4], out[5e-5]):
+        assert x["finite"] and y["finite"]
+        dv = (y["mean"]["rho_v"] - x["mean"]["rho_v"]) / x["mean"]["rho_v"]
+        dl = (y["mean"]["rho_l"] - x["mean"]["rho_l"]) / x["mean"]["rho_l"]
+        rows.append(dict(T0=T0, rho_v=x["mean"]["rho_v"], rho_l=x["mean"]["rho_l"], d_rho_v=dv, d_rho_l=dl))
+        print("T0=%.2f: rho_v %.6f rho_l %.6f (dt = 1e-4); dt/2 - dt: %+.2e %+.2e" %
+              (T0, x["mean"]["rho_v"], x["mean"]["rho_l"], dv, dl))
+    _dump("coexistence_fp64_half_dt", rows)
+    assert max(max(abs(r["d_rho_v"]), abs(r["d_rho_l"])) for r in rows) < 1e-4
 
 
 def laplace(fl, a, b, T, prec, t_end, radii=(20.0, 30.0, 40.0, 50.0)):
