@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<re
                                                        const real *__restrict__ kxt, KP<real> P, int with_grad) {
     using C = typename cplx_of<real>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ double red[6][NT];
+    __shared__ double red[6][NT / 32];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
     C *Wr = reinterpret_cast<C *>(smem_raw);
@@ -451,42 +451,45 @@ __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<re
         __syncthreads();
     }
     const real *g = reinterpret_cast<const real *>(buf);
-    double m = 0, px = 0, py = 0, e = 0, um = 0, bad = 0;
+    // per-site values in the working precision (no fp64 square roots or
+    // products for fp32 fields), sums in fp64
+    double m = 0, px = 0, py = 0, e = 0, bad = 0;
+    real um = 0;
     for (int x = tid; x < nx; x += NT) {
         const size_t s = (size_t)y * nx + x;
-        const double rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
-        double g2 = 0;
+        const real rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
+        real g2 = 0;
         if (with_grad) {
-            const double rx = g[x], ry = g[nx + x];
+            const real rx = g[x], ry = g[nx + x];
             g2 = rx * rx + ry * ry;
         }
-        const double u2 = ux * ux + uy * uy;
-        m += rho;
-        px += rho * ux;
-        py += rho * uy;
-        e += rho * T - (double)P.a * rho * rho + (double)P.K * g2 * 0.5 + rho * u2 * 0.5;
-        um = fmax(um, sqrt(u2));
-        const bool ok = isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(T) && rho > 0 && T > 0 &&
-                        (double)P.b * rho < 1.0;
+        const real u2 = ux * ux + uy * uy;
+        m += (double)rho;
+        px += (double)(rho * ux);
+        py += (double)(rho * uy);
+        e += (double)(rho * T - P.a * rho * rho + P.K * g2 * real(0.5) + rho * u2 * real(0.5));
+        um = um > sqrt(u2) ? um : sqrt(u2);
+        const bool ok = isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(T) && rho > real(0) && T > real(0) &&
+                        P.b * rho < real(1);
         bad += ok ? 0.0 : 1.0;
     }
-    red[0][tid] = m;
-    red[1][tid] = px;
-    red[2][tid] = py;
-    red[3][tid] = e;
-    red[4][tid] = um;
-    red[5][tid] = bad;
-    __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-        if (tid < w) {
-            for (int q = 0; q < 6; ++q) {
-                if (q == 4) red[q][tid] = fmax(red[q][tid], red[q][tid + w]);
-                else red[q][tid] += red[q][tid + w];
-            }
+    // block sums: warp shuffles, then one value per warp through shared memory
+    double v[6] = {m, px, py, e, (double)um, bad};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        for (int w = 16; w > 0; w >>= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, v[q], w);
+            v[q] = q == 4 ? fmax(v[q], o) : v[q] + o;
         }
-        __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0)
+        for (int q = 0; q < 6; ++q) red[q][warp] = v[q];
+    __syncthreads();
+    if (tid < 6) {
+        double acc = red[tid][0];
+        for (int w = 1; w < NT / 32; ++w) acc = tid == 4 ? fmax(acc, red[tid][w]) : acc + red[tid][w];
+        partial[(size_t)y * 6 + tid] = acc;
     }
-    if (tid < 6) partial[(size_t)y * 6 + tid] = red[tid][0];
 }
 
 static __global__ void k_reduce_partials(const double *partial, int ny, double *out) {

@@ -920,8 +920,7 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
                         st4(po + (size_t)(r0 + r) * N, fn);
                     }
                 }
-                continue;
-            }
+            } else {
 #pragma unroll(K5U)
             for (int s = 0; s < SMAX; ++s) {
                 const int x = tid + s * NT;
@@ -958,6 +957,7 @@ __global__ void __launch_bounds__(nt_k5wr<H>(), nt_k5wr<H>() >= 512 ? 1 : 2) k5_
                     if (with_base) fn += alpha * fb[r];
                     po[r * N] = fn;
                 }
+            }
             }
         }
         fence_proxy_async();
