@@ -424,50 +424,43 @@ __global__ void __launch_bounds__(NT) k_rows_inverse(const typename cplx_of<real
 template <typename real>
 __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<real>::type *spec,
                                                        const real *__restrict__ fields, double *partial,
-                                                       const typename cplx_of<real>::type *__restrict__ Wr_g,
-                                                       const typename cplx_of<real>::type *__restrict__ Wp_g,
                                                        const real *__restrict__ kxt, KP<real> P, int with_grad) {
     using C = typename cplx_of<real>::type;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ double red[6][NT / 32];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
     const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
-    C *Wr = reinterpret_cast<C *>(smem_raw);
-    C *Wp = Wr + h;
-    C *buf = Wp + h;   // [2][h]
+    // sum over the row of |grad rho|^2 by Parseval's relation from the row
+    // spectra, without inverse transforms: slot 0 holds Z = DFT_x rho (so
+    // D_x rho has spectrum i k_x Z, and k_x is zero at DC and at the row
+    // Nyquist bin), slot 2 holds Y = DFT_x(D_y rho) / nx from the column
+    // pass (its bin 0 packs the real DC and Nyquist values).  Over the
+    // two-sided spectrum, sum_x d^2 = (1 / nx) sum_k |DFT d|^2.
+    double gxs = 0, gys = 0;
     if (with_grad) {
-        load_tables(Wr, Wr_g, h);
-        load_tables(Wp, Wp_g, h);
-        // row 0: D_x rho = i k_x rho^ / nx from the row spectrum in slot 0;
-        // row 1: D_y rho from the column pass (slot 2)
-        const C *r0 = spec + (size_t)y * h, *r2 = spec + 2 * slot + (size_t)y * h;
+        const C *Z = spec + (size_t)y * h, *Y = spec + 2 * slot + (size_t)y * h;
         for (int k = tid; k < h; k += NT) {
-            const C z = r0[k];
-            const real m = kxt[k] * P.scale_x;
-            buf[k] = C{-m * z.y, m * z.x};
-            buf[(size_t)h + k] = r2[k];
+            const C z = Z[k], w = Y[k];
+            if (k == 0) {
+                gys += (double)(w.x * w.x) + (double)(w.y * w.y);
+            } else {
+                const real kx = kxt[k];
+                gxs += 2.0 * (double)(kx * kx * (z.x * z.x + z.y * z.y));
+                gys += 2.0 * (double)(w.x * w.x + w.y * w.y);
+            }
         }
-        rows_c2r(buf, h, 2, Wr, Wp);
-        __syncthreads();
     }
-    const real *g = reinterpret_cast<const real *>(buf);
     // per-site values in the working precision (no fp64 square roots or
     // products for fp32 fields), sums in fp64
-    double m = 0, px = 0, py = 0, e = 0, bad = 0;
+    double m = 0, px = 0, py = 0, e = 0.5 * (double)P.K * (gxs / nx + gys * nx), bad = 0;
     real um = 0;
     for (int x = tid; x < nx; x += NT) {
         const size_t s = (size_t)y * nx + x;
         const real rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
-        real g2 = 0;
-        if (with_grad) {
-            const real rx = g[x], ry = g[nx + x];
-            g2 = rx * rx + ry * ry;
-        }
         const real u2 = ux * ux + uy * uy;
         m += (double)rho;
         px += (double)(rho * ux);
         py += (double)(rho * uy);
-        e += (double)(rho * T - P.a * rho * rho + P.K * g2 * real(0.5) + rho * u2 * real(0.5));
+        e += (double)(rho * T - P.a * rho * rho + rho * u2 * real(0.5));
         um = um > sqrt(u2) ? um : sqrt(u2);
         const bool ok = isfinite(rho) && isfinite(ux) && isfinite(uy) && isfinite(T) && rho > real(0) && T > real(0) &&
                         P.b * rho < real(1);
@@ -2017,8 +2010,7 @@ class EngineT : public Engine {
             Status st = launch_col(inv_groups_, 1, false);
             if (!st.good()) return st;
         }
-        k_invariant_rows<real><<<ny_, NT, smem_inv_, stream_>>>(spec_, fields_, partial_, Wr_, Wp_, kxt_, kp_,
-                                                                with_grad ? 1 : 0);
+        k_invariant_rows<real><<<ny_, NT, 0, stream_>>>(spec_, fields_, partial_, kxt_, kp_, with_grad ? 1 : 0);
         FFTLB_LAUNCHED("k_invariant_rows");
         k_reduce_partials<<<1, NT, 0, stream_>>>(partial_, ny_, red_);
         FFTLB_LAUNCHED("k_reduce_partials");
