@@ -141,6 +141,26 @@ def test_convection_without_v_y_needs_no_column_pass(ring_speed):
         assert np.abs(row_inv(k1) - want).max() < 1e-9 * np.abs(want).max()
 
 
+def test_gradient_energy_by_parseval():
+    """The invariants' gradient energy (e_T of Eq. 17 holds K |grad rho|^2 /
+    2) as k_invariant_rows forms it: from the row spectrum Z of rho and the
+    column pass's Y = DFT_x(D_y rho) / nx, per row
+        (1 / nx) sum_{0<k<h} 2 k_x^2 |Z_k|^2 + nx (Y_0.x^2 + Y_0.y^2 + sum_{0<k<h} 2 |Y_k|^2),
+    against sum over the sites of (D_x rho)^2 + (D_y rho)^2 with the oracle's D."""
+    ny, nx, window, dx = 24, 32, 4, 1.0 / 64
+    rng = np.random.default_rng(5)
+    rho = 3.5 + rng.standard_normal((ny, nx))
+    h = nx // 2
+    kx = np.array([kappa_engine(j, nx, dx, window) for j in range(h + 1)])
+    ky = np.array([kappa_engine(j if j < ny // 2 else j - ny, ny, dx, window) for j in range(ny)])
+    Z = row_spec(rho)
+    Y = col_pass([(DY, Z)], kx, ky, 1.0 / (nx * ny))
+    gx = (2.0 * (kx[None, 1:h] ** 2) * np.abs(Z[:, 1:h]) ** 2).sum(axis=1) / nx
+    gy = nx * (Y[:, 0].real ** 2 + Y[:, 0].imag ** 2 + 2.0 * (np.abs(Y[:, 1:h]) ** 2).sum(axis=1))
+    want = O.D(rho, 'x', dx, window) ** 2 + O.D(rho, 'y', dx, window) ** 2
+    assert np.abs(gx + gy - want.sum(axis=1)).max() < 1e-9 * want.sum(axis=1).max()
+
+
 def test_planted_mistake_is_caught():
     """The same check fails when K3's Laplacian drops its k_x^2 term."""
     ny, nx, window, dx = 16, 32, 4, 1.0 / 64
