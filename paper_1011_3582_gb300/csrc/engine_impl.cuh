@@ -418,44 +418,56 @@ __global__ void __launch_bounds__(NT) k_rows_inverse(const typename cplx_of<real
     for (int x = tid; x < nx; x += NT) out[(size_t)fi * N + (size_t)y * nx + x] = (TOut)bre[x];
 }
 
-// Per-row fp64 partial sums for the invariants: mass, momentum, e_T
-// (Eq. 17, grad rho from spectrum slots 1 and 2), max |u|, and a count of
-// non-finite or unphysical sites.  grid = ny.
+// Invariant sums, first pass (grid = ny, one block per row y): the moments
+// (Eqs. 7-9) of the row into fields, and the row's fp64 partial sums of
+// mass, momentum, e_T of Eq. 17 without its gradient part, max |u| and the
+// count of non-finite or unphysical sites.  With with_grad, also the
+// forward row transform of rho into spectrum slot 0 and the row's
+// x-gradient energy sum_x (D_x rho)^2 by Parseval's relation: slot 0 holds
+// Z = DFT_x rho, D_x rho has spectrum i k_x Z (k_x is zero at DC and at the
+// row Nyquist bin), and over the two-sided spectrum sum_x d^2 =
+// (1 / nx) sum_k |DFT d|^2.  partial[8 y + 0..7] = mass, px, py, e_T
+// part, max |u|, count, x-gradient energy, 0 (k_inv_grad_y fills 7).
+// Per-site values in the working precision (no fp64 square roots or
+// products for fp32 fields), sums in fp64.
 template <typename real>
-__global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<real>::type *spec,
-                                                       const real *__restrict__ fields, double *partial,
-                                                       const real *__restrict__ kxt, KP<real> P, int with_grad) {
+__global__ void __launch_bounds__(NT) k_inv_rows(const real *__restrict__ f, real *__restrict__ fields,
+                                                 typename cplx_of<real>::type *spec, double *partial,
+                                                 const typename cplx_of<real>::type *__restrict__ Wr_g,
+                                                 const typename cplx_of<real>::type *__restrict__ Wp_g,
+                                                 const real *__restrict__ kxt, KP<real> P, int with_grad) {
     using C = typename cplx_of<real>::type;
-    __shared__ double red[6][NT / 32];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ double red[7][NT / 32];
     const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
-    const size_t N = (size_t)nx * ny, slot = (size_t)ny * h;
-    // sum over the row of |grad rho|^2 by Parseval's relation from the row
-    // spectra, without inverse transforms: slot 0 holds Z = DFT_x rho (so
-    // D_x rho has spectrum i k_x Z, and k_x is zero at DC and at the row
-    // Nyquist bin), slot 2 holds Y = DFT_x(D_y rho) / nx from the column
-    // pass (its bin 0 packs the real DC and Nyquist values).  Over the
-    // two-sided spectrum, sum_x d^2 = (1 / nx) sum_k |DFT d|^2.
-    double gxs = 0, gys = 0;
+    const size_t N = (size_t)nx * ny;
+    C *Wr = reinterpret_cast<C *>(smem_raw);
+    C *Wp = Wr + h;
+    C *buf = Wp + h;
+    real *bre = reinterpret_cast<real *>(buf);
     if (with_grad) {
-        const C *Z = spec + (size_t)y * h, *Y = spec + 2 * slot + (size_t)y * h;
-        for (int k = tid; k < h; k += NT) {
-            const C z = Z[k], w = Y[k];
-            if (k == 0) {
-                gys += (double)(w.x * w.x) + (double)(w.y * w.y);
-            } else {
-                const real kx = kxt[k];
-                gxs += 2.0 * (double)(kx * kx * (z.x * z.x + z.y * z.y));
-                gys += 2.0 * (double)(w.x * w.x + w.y * w.y);
-            }
-        }
+        load_tables(Wr, Wr_g, h);
+        load_tables(Wp, Wp_g, h);
     }
-    // per-site values in the working precision (no fp64 square roots or
-    // products for fp32 fields), sums in fp64
-    double m = 0, px = 0, py = 0, e = 0.5 * (double)P.K * (gxs / nx + gys * nx), bad = 0;
+    double m = 0, px = 0, py = 0, e = 0, bad = 0;
     real um = 0;
     for (int x = tid; x < nx; x += NT) {
         const size_t s = (size_t)y * nx + x;
-        const real rho = fields[s], ux = fields[N + s], uy = fields[2 * N + s], T = fields[3 * N + s];
+        real m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        for (int i = 0; i < Q; ++i) {
+            const real v = f[(size_t)i * N + s];
+            m0 += v;
+            m1 += VX<real>(i) * v;
+            m2 += VY<real>(i) * v;
+            m3 += V2<real>(i) * v;
+        }
+        const real rho = m0, ux = m1 / m0, uy = m2 / m0;
+        const real T = real(0.5) * (m3 / m0 - (ux * ux + uy * uy));
+        fields[s] = rho;
+        fields[N + s] = ux;
+        fields[2 * N + s] = uy;
+        fields[3 * N + s] = T;
+        if (with_grad) bre[x] = rho;
         const real u2 = ux * ux + uy * uy;
         m += (double)rho;
         px += (double)(rho * ux);
@@ -466,44 +478,92 @@ __global__ void __launch_bounds__(NT) k_invariant_rows(const typename cplx_of<re
                         P.b * rho < real(1);
         bad += ok ? 0.0 : 1.0;
     }
+    double gxs = 0;
+    if (with_grad) {
+        rows_r2c(buf, h, 1, Wr, Wp);   // (barriers before and after)
+        C *dst = spec + (size_t)y * h;
+        for (int k = tid; k < h; k += NT) {
+            const C z = buf[k];
+            dst[k] = z;
+            if (k > 0) {
+                const real kx = kxt[k];
+                gxs += 2.0 * (double)(kx * kx * (z.x * z.x + z.y * z.y));
+            }
+        }
+        gxs /= nx;
+    }
     // block sums: warp shuffles, then one value per warp through shared memory
-    double v[6] = {m, px, py, e, (double)um, bad};
+    double v[7] = {m, px, py, e, (double)um, bad, gxs};
 #pragma unroll
-    for (int q = 0; q < 6; ++q)
+    for (int q = 0; q < 7; ++q)
         for (int w = 16; w > 0; w >>= 1) {
             const double o = __shfl_down_sync(0xffffffffu, v[q], w);
             v[q] = q == 4 ? fmax(v[q], o) : v[q] + o;
         }
     const int warp = tid >> 5, lane = tid & 31;
     if (lane == 0)
-        for (int q = 0; q < 6; ++q) red[q][warp] = v[q];
+        for (int q = 0; q < 7; ++q) red[q][warp] = v[q];
     __syncthreads();
-    if (tid < 6) {
-        double acc = red[tid][0];
-        for (int w = 1; w < NT / 32; ++w) acc = tid == 4 ? fmax(acc, red[tid][w]) : acc + red[tid][w];
-        partial[(size_t)y * 6 + tid] = acc;
+    if (tid < 8) {
+        double acc = 0;
+        if (tid < 7) {
+            acc = red[tid][0];
+            for (int w = 1; w < NT / 32; ++w) acc = tid == 4 ? fmax(acc, red[tid][w]) : acc + red[tid][w];
+        }
+        partial[(size_t)y * 8 + tid] = acc;
     }
 }
 
-static __global__ void k_reduce_partials(const double *partial, int ny, double *out) {
-    __shared__ double red[6][NT];
+// Invariant sums, second pass (grid = ny): the row's y-gradient energy
+// sum_x (D_y rho)^2 by Parseval's relation from Y = DFT_x(D_y rho) / nx in
+// spectrum slot 2 (the column pass's output; bin 0 packs the real DC and
+// Nyquist values): nx (Y_0.x^2 + Y_0.y^2 + sum_{0<k<h} 2 |Y_k|^2), into
+// partial[8 y + 7].
+template <typename real>
+__global__ void __launch_bounds__(NT) k_inv_grad_y(const typename cplx_of<real>::type *spec, double *partial,
+                                                   KP<real> P) {
+    using C = typename cplx_of<real>::type;
+    __shared__ double red[NT / 32];
+    const int nx = P.nx, ny = P.ny, h = P.h, y = blockIdx.x, tid = threadIdx.x;
+    const size_t slot = (size_t)ny * h;
+    const C *Y = spec + 2 * slot + (size_t)y * h;
+    double g = 0;
+    for (int k = tid; k < h; k += NT) {
+        const C w = Y[k];
+        g += k == 0 ? (double)(w.x * w.x) + (double)(w.y * w.y) : 2.0 * (double)(w.x * w.x + w.y * w.y);
+    }
+    for (int w = 16; w > 0; w >>= 1) g += __shfl_down_sync(0xffffffffu, g, w);
+    if ((tid & 31) == 0) red[tid >> 5] = g;
+    __syncthreads();
+    if (tid == 0) {
+        double acc = 0;
+        for (int w = 0; w < NT / 32; ++w) acc += red[w];
+        partial[(size_t)y * 8 + 7] = acc * nx;
+    }
+}
+
+// The invariants from the per-row partials of k_inv_rows / k_inv_grad_y:
+// out[0..5] = mass, px, py, e_T (with K / 2 times the gradient energy),
+// max |u|, count.
+static __global__ void k_reduce_partials(const double *partial, int ny, double K, double *out) {
+    __shared__ double red[8][NT];
     const int tid = threadIdx.x;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int y = tid; y < ny; y += NT) {
-        for (int q = 0; q < 6; ++q) {
-            const double v = partial[(size_t)y * 6 + q];
+        for (int q = 0; q < 8; ++q) {
+            const double v = partial[(size_t)y * 8 + q];
             acc[q] = (q == 4) ? fmax(acc[q], v) : acc[q] + v;
         }
     }
-    for (int q = 0; q < 6; ++q) red[q][tid] = acc[q];
+    for (int q = 0; q < 8; ++q) red[q][tid] = acc[q];
     __syncthreads();
     for (int w = NT / 2; w > 0; w >>= 1) {
         if (tid < w)
-            for (int q = 0; q < 6; ++q)
+            for (int q = 0; q < 8; ++q)
                 red[q][tid] = (q == 4) ? fmax(red[q][tid], red[q][tid + w]) : red[q][tid] + red[q][tid + w];
         __syncthreads();
     }
-    if (tid < 6) out[tid] = red[tid][0];
+    if (tid < 6) out[tid] = tid == 3 ? red[3][0] + 0.5 * K * (red[6][0] + red[7][0]) : red[tid][0];
 }
 
 }  // namespace fftlb
@@ -983,7 +1043,7 @@ class EngineT : public Engine {
         if (!(st = dalloc(&Wr_, (size_t)h_)).good()) return st;
         if (!(st = dalloc(&Wp_, (size_t)h_)).good()) return st;
         if (!(st = dalloc(&Wc_, (size_t)ny_)).good()) return st;
-        if (!(st = dalloc(&partial_, (size_t)ny_ * 6)).good()) return st;
+        if (!(st = dalloc(&partial_, (size_t)ny_ * 8)).good()) return st;
         if (!(st = dalloc(&red_, 8)).good()) return st;
         if (!(st = dalloc(&err_, 4)).good()) return st;
         FFTLB_CU(cudaMemset(err_, 0, 4 * sizeof(int)));
@@ -1257,7 +1317,7 @@ class EngineT : public Engine {
         }
         // invariants: rho in slot 0 -> D_y rho in slot 2 (one input, one
         // output: the convection kernels; D_x rho is formed in the row
-        // spectrum by k_invariant_rows)
+        // spectrum by k_inv_rows)
         inv_groups_ = (int)gs.size();
         {
             GroupDesc g = group(1, 0, 0);
@@ -1296,6 +1356,7 @@ class EngineT : public Engine {
         if (smem_col2_ > budget || smem_inv_ > budget)
             return Status::err(FFTLB_ERR_ARG, "grid too large for shared-memory tiles");
         FFTLB_CU(cudaFuncSetAttribute(k_col<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
+        FFTLB_CU(cudaFuncSetAttribute(k_inv_rows<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
         kp_.nx = nx_;
         kp_.ny = ny_;
         kp_.h = h_;
@@ -2002,17 +2063,16 @@ class EngineT : public Engine {
     // (one synchronisation: the sums and the device error word of the steps
     // before them come back together)
     Status sums(bool with_grad, double out[6]) {
-        k_moments<real><<<grid1d(), 256, 0, stream_>>>(f0_, fields_, N_);
-        FFTLB_LAUNCHED("k_moments");
+        k_inv_rows<real><<<ny_, NT, with_grad ? smem_rows1_ : 0, stream_>>>(f0_, fields_, spec_, partial_, Wr_, Wp_,
+                                                                          kxt_, kp_, with_grad ? 1 : 0);
+        FFTLB_LAUNCHED("k_inv_rows");
         if (with_grad) {
-            k_rows_forward<real, real><<<dim3(ny_, 1), NT, smem_rows1_, stream_>>>(fields_, spec_, 0, Wr_, Wp_, kp_);
-            FFTLB_LAUNCHED("k_rows_forward");
             Status st = launch_col(inv_groups_, 1, false);
             if (!st.good()) return st;
+            k_inv_grad_y<real><<<ny_, NT, 0, stream_>>>(spec_, partial_, kp_);
+            FFTLB_LAUNCHED("k_inv_grad_y");
         }
-        k_invariant_rows<real><<<ny_, NT, 0, stream_>>>(spec_, fields_, partial_, kxt_, kp_, with_grad ? 1 : 0);
-        FFTLB_LAUNCHED("k_invariant_rows");
-        k_reduce_partials<<<1, NT, 0, stream_>>>(partial_, ny_, red_);
+        k_reduce_partials<<<1, NT, 0, stream_>>>(partial_, ny_, (double)p_.K, red_);
         FFTLB_LAUNCHED("k_reduce_partials");
         int e = 0;
         FFTLB_CU(cudaMemcpyAsync(out, red_, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
