@@ -16,8 +16,8 @@ acoustic oscillations the initial profiles launch decay only on the
 viscous time L^2 / nu (see paper_1011_3582_gb300.physics).
 
 The short test runs in the normal GPU suite; the long experiments run only
-with FFTLB_PHYSICS=1 (several GPU-minutes) and print the tables quoted in
-the design notes (FFTLB_PHYSICS_OUT=<file> also writes them as JSON)."""
+with FFTLB_PHYSICS=1 (several GPU-minutes) and print their tables
+(FFTLB_PHYSICS_OUT=<file> also writes them as JSON)."""
 import json
 import os
 
