@@ -82,3 +82,25 @@ def test_column_tile_layout(NY):
                 assert col == c
                 assert (c + TW * reader_l) // 32 == (c + TW * l) // 32
     assert M.worst_conflict_sets(M.col_access_sets(NY)) == 1
+
+
+@pytest.mark.parametrize("H", [512, 256, 128])
+def test_row_spectrum_times_ik(H):
+    """r2c_post_wr2 (the separable split's row-spectrum derivative): its raw
+    output is r2c_post_wr's, and the inverse of its i k_x X / nx output is
+    the spectral x-derivative of the row (k_x zero at DC and Nyquist)."""
+    rng = np.random.default_rng(H + 1)
+    x = rng.standard_normal(2 * H)
+    nx, dx = 2 * H, 1.0 / 64
+    kxt = 2 * np.pi * np.arange(H + 1) / (nx * dx)
+    kxt[H] = 0.0
+    Z = M.row_fft_wr(x[0::2] + 1j * x[1::2], H, -1)
+    raw, mul = M.r2c_post2(Z, H, kxt, 1.0 / nx)
+    assert np.allclose(raw, M.r2c_post(Z, H))
+    z = M.row_fft_wr(M.c2r_pre(mul, H), H, +1)
+    d = np.empty(nx)
+    d[0::2], d[1::2] = z.real, z.imag
+    k = 2 * np.pi * np.arange(H + 1) / (nx * dx)
+    k[H] = 0.0
+    want = np.fft.irfft(1j * k * np.fft.rfft(x), n=nx)
+    assert np.abs(d - want).max() < 1e-9 * np.abs(want).max()

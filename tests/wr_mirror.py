@@ -130,6 +130,31 @@ def r2c_post(Z, H):
     return out
 
 
+def r2c_post2(Z, H, kxt, sx):
+    """Emulates r2c_post_wr2: the one-sided spectrum X as r2c_post_wr writes
+    it (raw) and i k_x X / nx (mul, sx = 1 / nx), pair by pair (k, H - k) as
+    the lanes take them, k_x looked up at both bins of the pair."""
+    raw = np.zeros(H, complex)
+    mul = np.zeros(H, complex)
+    Wp = np.exp(-2j * np.pi * np.arange(H // 2 + 1) / (2 * H))
+    for k in range(H // 2 + 1):
+        if k == 0:
+            a = complex(Z[0].real + Z[0].imag, Z[0].real - Z[0].imag)
+            b = None
+        else:
+            p, q = Z[k], Z[H - k]
+            ze = 0.5 * (p + np.conj(q))
+            zo = -0.5j * (p - np.conj(q))
+            wz = Wp[k] * zo
+            a, b = ze + wz, np.conj(ze - wz)
+        raw[k] = a
+        mul[k] = 1j * (kxt[k] * sx) * a
+        if k != 0 and H - k != k:
+            raw[H - k] = b
+            mul[H - k] = 1j * (kxt[H - k] * sx) * b
+    return raw, mul
+
+
 def c2r_pre(X, H):
     """Emulates c2r_pre_wr."""
     z = X.astype(complex).copy()
