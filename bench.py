@@ -327,7 +327,9 @@ class Replicas:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    # (600 steps: about 0.6 s timed at 1024^2, long enough for the 100 ms
+    # clock sampler to see at least three samples inside the timed region)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
