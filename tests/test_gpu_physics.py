@@ -181,14 +181,16 @@ def test_coexistence_gradient_coefficient(fl):
     densities at the measured temperature (the K = 1e-5 runs are
     test_coexistence_fp32).  With K = 0 nothing sets an interface width: the
     profile steepens to the grid scale, where the windowed derivative's
-    error is largest, so the run is reported, finite or not."""
+    error is largest, so the run is reported, finite or not.  With
+    FFTLB_PHYSICS_FP64=1 the K = 5e-6 runs are made in fp64."""
     out = {}
-    for K in (5e-6, 0.0):
+    prec = 64 if os.environ.get("FFTLB_PHYSICS_FP64") else 32   # fp64: the reference of the fp32 error
+    for K in ((5e-6,) if prec == 64 else (5e-6, 0.0)):
         runs = []
         for T in (0.87, 0.89, 0.91, 0.93, 0.95, 0.97):
             rv, rl = TH.maxwell(T, 9 / 8, 1 / 3)
             fields = W.slab(512, 4, rv, rl, T, width=2.0, axis="x")
-            p = fl.params(nx=512, ny=4, a=9 / 8, b=1 / 3, K=K, dt=1e-4, precision=32, integrator=3)
+            p = fl.params(nx=512, ny=4, a=9 / 8, b=1 / 3, K=K, dt=1e-4, precision=prec, integrator=3)
             runs.append(PH.Run(p, fields, "slab", "x"))
         res = PH.relax(fl, runs, t_end=8.0, sample_dt=0.1)
         rows = []
@@ -203,7 +205,7 @@ def test_coexistence_gradient_coefficient(fl):
             print("K=%g T0=%.2f T=%.5f rho_v=%.6f rho_l=%.6f dev %+.2e %+.2e umax %.2e"
                   % (K, T, Tm, r["mean"]["rho_v"], r["mean"]["rho_l"], ev, el, r["mean"]["umax"]))
         out[str(K)] = rows
-    _dump("coexistence_K", out)
+    _dump("coexistence_K_fp%d" % prec, out)
     assert all(r["finite"] for r in out[str(5e-6)])
 
 
